@@ -1,0 +1,192 @@
+/*
+ * lbmpen — GB300-native constraint-penalization lattice Boltzmann method for
+ * rigid particles in fluid (Millet & Liberge, arXiv 2511.01629).
+ *
+ * C ABI of the hot path.  One time step of one lattice instance (Sec. 2):
+ *   1. pull streaming with halfway bounce-back walls (left side of Eq. 10);
+ *   2. moments u, p (Eq. 15) with the node's acceleration f/rho;
+ *   3. solid indicator chi (Eq. 9) of every particle;
+ *   4. BGK collision with Guo forcing (Eqs. 10, 13, 14) and, on solid nodes,
+ *      the penalization source S = w/(2 cs^4) alpha Pi_neq : (c c - cs^2 I)
+ *      (Eq. 17);
+ *   5. per-particle rigid-body projection U, omega over each solid domain
+ *      (Eq. 22) from in-kernel partial sums, reduced in a fixed order;
+ *   6. particle update: repulsive collision forces (Eqs. 19-21) and the
+ *      predictor-corrector of Algorithm 1, which also yields the collision
+ *      acceleration A applied on the particle's nodes in the next step.
+ * Steps 1-5 run in one fused CUDA kernel per step over all instances; step 6
+ * runs in FP64 in small per-particle kernels.
+ *
+ * Units: lattice units, dx = dt = 1 (Sec. 3 preamble).  Node (i, j, k) sits at
+ * integer coordinates; fields are row-major with x fastest.
+ *
+ * Lattices and population numbering (used by lbm_set/get_populations):
+ *   D2Q9 : 0 rest; 1 +x; 2 +y; 3 -x; 4 -y; 5 (1,1); 6 (-1,1); 7 (-1,-1);
+ *          8 (1,-1)  (the paper's Fig. 1); weights 4/9, 1/9, 1/36 by |c|.
+ *   D3Q19: 0 rest; 1 +x; 2 -x; 3 +y; 4 -y; 5 +z; 6 -z; 7 (1,1,0);
+ *          8 (-1,-1,0); 9 (1,-1,0); 10 (-1,1,0); 11 (1,0,1); 12 (-1,0,-1);
+ *          13 (1,0,-1); 14 (-1,0,1); 15 (0,1,1); 16 (0,-1,-1); 17 (0,1,-1);
+ *          18 (0,-1,1); weights 1/3, 1/18, 1/36.
+ * The rest population of this zero-shifted velocity model (Eq. 13) never
+ * enters u, p (Eq. 15), Pi_neq or any other population, so the library does
+ * not store it: lbm_get_populations returns 0 for it and lbm_set_populations
+ * ignores it.
+ *
+ * Errors: every call returns an lbm_status; nothing aborts or throws across
+ * the ABI.  Device-side failures (divergence, list overflow, a particle
+ * leaving the box) are recorded in a device status word and surface at the
+ * next lbm_sync (or any call that synchronises).  After an error the message
+ * is available from lbm_last_error.  A context is not thread-safe.
+ *
+ * Memory: the context owns its device memory, taken from the caller's
+ * allocator (or cudaMalloc when none is given) and returned in lbm_destroy.
+ * The caller owns every array passed in; inputs are copied, outputs written.
+ * All work is issued on the stream given at creation.
+ */
+#ifndef LBMPEN_H
+#define LBMPEN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = -1,   /* bad argument or configuration */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,       /* device allocation failed */
+    LBM_ERR_DIVERGED = -4,  /* |u| >= 0.5 or non-finite velocity on some node */
+    LBM_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+    LBM_ERR_STATE = -6,     /* context unusable (destroyed, failed before) */
+    LBM_ERR_CAPACITY = -7,  /* more particles overlap a tile than it can list */
+    LBM_ERR_PARTICLE = -8   /* a particle centre crossed a wall */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+enum { LBM_FP32 = 0, LBM_FP16 = 1 };
+enum { LBM_PERIODIC = 0, LBM_WALL = 1 };
+
+/* One lattice instance (Sec. 2.2-2.4; the collision parameters follow
+ * Eqs. 19-20 and Algorithm 1).  Fill with lbm_config_default first. */
+typedef struct {
+    int lattice;             /* LBM_D2Q9 or LBM_D3Q19 */
+    int storage;             /* LBM_FP32 or LBM_FP16 population storage; compute is FP32 */
+    int n[3];                /* nodes per axis; n[2] = 1 for D2Q9 */
+    int bc[3];               /* per axis: LBM_PERIODIC, or LBM_WALL (both faces) */
+    double wall_u[3][2][3];  /* velocity of wall (axis, face 0 = low / 1 = high); it must be
+                                tangential, and a moving wall needs every other axis periodic */
+    double tau;              /* BGK relaxation time tau > 1/2 (Eq. 10) */
+    double alpha;            /* penalty coefficient (Eq. 17); default 1/tau (Sec. 3) */
+    double rho_f;            /* fluid density; default 1 */
+    double g_drive[3];       /* body acceleration on every node (channel driving) */
+    double g_grav[3];        /* gravity: on solid nodes (1 - rho_f/rho_s) g, none on fluid */
+    double delta;            /* collision range delta (Eqs. 19-20); default 1 */
+    double eps_p, eps_w;     /* stiffnesses epsilon_p, epsilon_w; defaults 2 and 1 */
+    int K;                   /* predictor-corrector sub-steps (Algorithm 1); default 1 */
+    int max_particles;       /* capacity reserved at creation; default 64 */
+    double max_radius;       /* largest particle radius to be added; default 16 */
+    int fp16_scale_log2;     /* FP16 storage keeps f * 2^k (exact scaling); default 14 */
+} lbm_config;
+
+/* Device memory callbacks.  alloc returns NULL on failure.  Both run on the
+ * host; stream is the context's cudaStream_t. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} lbm_allocator;
+
+/* Fill cfg with defaults for a box of the given size: walls on every axis,
+ * tau = 1, alpha = 1/tau, no forces, FP32 storage. */
+int lbm_config_default(lbm_config* cfg, int lattice, int nx, int ny, int nz);
+
+/* Create a context holding one instance.  stream: cudaStream_t (NULL = the
+ * legacy default stream).  On success *out owns the device state.  The fluid
+ * starts at rest (f = 0; Eq. 13 gives feq(0, 0) = 0). */
+int lbm_create(const lbm_config* cfg, const lbm_allocator* alloc, void* stream, lbm_ctx** out);
+
+/* Create one context over n independent instances of possibly different
+ * sizes and particle counts.  lbm_step advances all of them with one fused
+ * fluid launch per step over a work list of every instance's tiles.  All
+ * instances must share lattice and storage. */
+int lbm_create_batch(const lbm_config* cfgs, int n, const lbm_allocator* alloc, void* stream,
+                     lbm_ctx** out);
+
+int lbm_num_instances(const lbm_ctx* ctx);
+
+/* Add n particles (disks in 2D, spheres in 3D) to an instance.
+ *   pos   n*D centres (lattice units), radius n radii (>= 2, <= max_radius),
+ *   density_ratio n values of rho_s / rho_f,
+ *   vel   n*D initial velocities or NULL (zero); it is U^{-1} of Algorithm 1,
+ *   omega n (2D) or n*3 (3D) initial angular velocities or NULL.
+ * Valid before the first step and between steps.  Fails with
+ * LBM_ERR_INVALID when a centre lies outside the box on a wall axis, a radius
+ * is out of range or the capacity would be exceeded. */
+int lbm_add_particles(lbm_ctx* ctx, int instance, int n, const double* pos, const double* radius,
+                      const double* density_ratio, const double* vel, const double* omega);
+
+/* Advance every instance by nsteps time steps.  Asynchronous on the context
+ * stream; device errors surface at the next lbm_sync.  After the first call
+ * the steps are replayed from captured CUDA graphs unless graphs are off. */
+int lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Wait for the context stream and report the device status word. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields of the current state, i.e. what the next step sees
+ * (streaming and Eq. 15 without collision):
+ *   u     D*N floats, [d][z][y][x], or NULL;  p  N floats or NULL;
+ *   owner N ints: particle index owning the node, -1 for fluid, or NULL.
+ * on_device: 1 if the pointers are device memory, 0 for host memory
+ * (then the call synchronises). */
+int lbm_get_fields(lbm_ctx* ctx, int instance, float* u, float* p, int* owner, int on_device);
+
+/* Particle state after the last step (host arrays, any may be NULL; the call
+ * synchronises): pos X^{n+1} (n*D), vel U^n (n*D), omega omega^n (n or n*3),
+ * theta orientation (n or n*3; trapezoidal integral of omega), accel A^{n+1}
+ * (n*D), count = solid nodes at step n (n). */
+int lbm_get_particles(lbm_ctx* ctx, int instance, double* pos, double* vel, double* omega,
+                      double* theta, double* accel, int* count);
+int lbm_num_particles(const lbm_ctx* ctx, int instance);
+
+/* Populations f* after the last collision, Q*N floats [q][z][y][x] in the
+ * numbering above (host or device memory; the set call accepts FP32 values
+ * and rounds them to the storage precision). */
+int lbm_set_populations(lbm_ctx* ctx, int instance, const float* f, int on_device);
+int lbm_get_populations(lbm_ctx* ctx, int instance, float* f, int on_device);
+
+/* Checkpoint: the complete state of every instance (populations in storage
+ * precision, FP64 particle state, step counter) as one opaque host buffer.
+ * Call save with buf = NULL to query *bytes. */
+int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes);
+int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Tuning and introspection. */
+int lbm_set_graphs(lbm_ctx* ctx, int steps_per_graph); /* 0 = plain launches */
+/* Time each fluid-kernel shape on the current state and keep the fastest.
+ * The state is not changed.  reps: timed launches per shape. */
+int lbm_autotune(lbm_ctx* ctx, int reps);
+/* Current fluid-kernel shape: nodes per thread, tile rows, warps per block. */
+int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);
+int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
+/* Kernel launches issued by one lbm_step(ctx, 1) (fluid + particle kernels). */
+int lbm_launches_per_step(const lbm_ctx* ctx);
+/* Fluid kernel alone, one launch, for timing: advances the populations of
+ * every instance by one step exactly as lbm_step does (particles are not
+ * moved).  Returns after enqueueing. */
+int lbm_fluid_step_only(lbm_ctx* ctx);
+long long lbm_steps_done(const lbm_ctx* ctx);
+long long lbm_total_nodes(const lbm_ctx* ctx);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(int status);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

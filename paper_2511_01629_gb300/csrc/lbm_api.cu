@@ -1,0 +1,961 @@
+// Host side of the lbmpen C ABI (declared in include/lbmpen.h): context and
+// device-memory management, launch sequencing, CUDA-graph replay of the step
+// loop, the fluid-kernel autotuner and state import/export.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmpen.h"
+#include "lbm_internal.cuh"
+
+namespace lbmpen {
+cudaError_t launch_fluid(int Q, int fp16, const InstDesc* insts, const uint16_t* tile_inst,
+                         int ntiles, int par, const Shape& sh, int commit, int persistent, int grid,
+                         int* tile_ctr, cudaStream_t st);
+int fluid_max_blocks_per_sm(int Q, int fp16, const Shape& sh);
+cudaError_t launch_fields(int Q, int fp16, const InstDesc* insts, int inst, long long N, int par,
+                          const Shape& sh, float* u, float* p, int* owner, cudaStream_t st);
+cudaError_t launch_pack(int Q, int fp16, const InstDesc* insts, int inst, long long N, int par,
+                        const float* src, cudaStream_t st);
+cudaError_t launch_unpack(int Q, int fp16, const InstDesc* insts, int inst, long long N, int par,
+                          float* dst, cudaStream_t st);
+cudaError_t launch_finalize(const InstDesc* insts, const PartRef* refs, int ntotal, int D,
+                            cudaStream_t st);
+cudaError_t launch_substep(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int src,
+                           int K, int last, int lpar, const Shape& sh, cudaStream_t st);
+cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int lpar,
+                           const Shape& sh, cudaStream_t st);
+}  // namespace lbmpen
+
+using namespace lbmpen;
+
+namespace {
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Instance {
+    lbm_config cfg;
+    int n[3];
+    int pitch = 0;
+    long long qstride = 0;
+    int np = 0, cap = 0;
+    int ntile[3] = {1, 1, 1};
+    int ntiles = 0, tile0 = 0;
+    int maxk = 0;
+    DevBuf f[2], prec, lcnt[2], lent[2], partial, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk,
+        Ubar, Xf;
+    std::vector<double> hR;  // radii (validation)
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int Q = 9, D = 2, fp16 = 0;
+    cudaStream_t st = nullptr;
+    lbm_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<Instance> inst;
+    DevBuf d_insts, d_tile_inst, d_tile_ctr, d_status, d_refs;
+    int ntiles = 0, np_total = 0;
+    int par = 0;
+    long long steps = 0;
+    Shape shape{4, 4, 1, 4, 0};
+    int grid = 0, num_sms = 0;
+    int graph_steps = 16;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    bool graph_ok[2] = {false, false};
+    bool failed = false;
+    std::string err;
+};
+
+namespace {
+
+int set_err(lbm_ctx* c, int code, const char* fmt, const char* detail = "") {
+    if (c) {
+        char buf[512];
+        snprintf(buf, sizeof buf, fmt, detail);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_err(lbm_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBM_OK;
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call);     \
+    } while (0)
+
+int dalloc(lbm_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (b.ptr && b.bytes >= bytes) return LBM_OK;
+    if (b.ptr) {
+        if (ctx->has_alloc) ctx->alloc.free(b.ptr, b.bytes, ctx->st, ctx->alloc.user);
+        else cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (ctx->has_alloc) p = ctx->alloc.alloc(bytes, ctx->st, ctx->alloc.user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (!p) return set_err(ctx, LBM_ERR_OOM, "device allocation of %s bytes failed",
+                           std::to_string(bytes).c_str());
+    b.ptr = p;
+    b.bytes = bytes;
+    return LBM_OK;
+}
+
+void dfree(lbm_ctx* ctx, DevBuf& b) {
+    if (!b.ptr) return;
+    if (ctx->has_alloc) ctx->alloc.free(b.ptr, b.bytes, ctx->st, ctx->alloc.user);
+    else cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+template <class T> T* P(const DevBuf& b) { return static_cast<T*>(b.ptr); }
+
+int validate(const lbm_config* c, char* why, size_t nwhy) {
+    auto bad = [&](const char* m) {
+        snprintf(why, nwhy, "%s", m);
+        return 0;
+    };
+    if (c->lattice != LBM_D2Q9 && c->lattice != LBM_D3Q19) return bad("lattice must be 9 or 19");
+    if (c->storage != LBM_FP32 && c->storage != LBM_FP16) return bad("storage must be FP32 or FP16");
+    const int D = c->lattice == LBM_D2Q9 ? 2 : 3;
+    for (int d = 0; d < D; ++d)
+        if (c->n[d] < 2 || c->n[d] > (1 << 20)) return bad("each axis needs 2 .. 2^20 nodes");
+    if (D == 2 && c->n[2] != 1) return bad("D2Q9 needs n[2] = 1");
+    if (!(c->tau > 0.5) || !(c->tau < 100.0)) return bad("tau must lie in (0.5, 100)");
+    if (!(c->alpha >= 0.0) || c->alpha * c->tau > 1.0 + 1e-12)
+        return bad("alpha must lie in [0, 1/tau]");
+    if (!(c->rho_f > 0)) return bad("rho_f must be positive");
+    if (!(c->delta > 0) || !(c->eps_p > 0) || !(c->eps_w > 0))
+        return bad("delta, eps_p and eps_w must be positive");
+    if (c->K < 1 || c->K > 64) return bad("K must lie in 1 .. 64");
+    if (c->max_particles < 0 || c->max_particles > (1 << 20)) return bad("max_particles out of range");
+    if (!(c->max_radius >= 2.0)) return bad("max_radius must be >= 2");
+    if (c->fp16_scale_log2 < 0 || c->fp16_scale_log2 > 24) return bad("fp16_scale_log2 in 0 .. 24");
+    for (int d = 0; d < 3; ++d) {
+        if (c->bc[d] != LBM_PERIODIC && c->bc[d] != LBM_WALL) return bad("bc must be PERIODIC or WALL");
+        for (int f = 0; f < 2; ++f) {
+            const double* u = c->wall_u[d][f];
+            bool moving = u[0] != 0 || u[1] != 0 || u[2] != 0;
+            if (!moving) continue;
+            if (d >= D || c->bc[d] != LBM_WALL) return bad("wall velocity on a non-wall face");
+            if (u[d] != 0) return bad("wall velocity must be tangential");
+            for (int e = 0; e < D; ++e)
+                if (e != d && c->bc[e] != LBM_PERIODIC)
+                    return bad("a moving wall needs every other axis periodic");
+        }
+    }
+    return 1;
+}
+
+int max_slots(const Instance& I, int D, const Shape& sh) {
+    const int T[3] = {32 * sh.vec, sh.ty, sh.tz};
+    int k = 1;
+    for (int d = 0; d < D; ++d) {
+        const int span = (int)ceil(2 * I.cfg.max_radius) + 4;
+        k *= std::min(span / T[d] + 2, I.ntile[d]);
+    }
+    return std::min(std::max(k, 1), MAXK);
+}
+
+InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
+    InstDesc d{};
+    const lbm_config& c = I.cfg;
+    for (int a = 0; a < 3; ++a) {
+        d.n[a] = I.n[a];
+        d.periodic[a] = (a >= ctx->D) ? 1 : (c.bc[a] == LBM_PERIODIC);
+        d.ntile[a] = I.ntile[a];
+        d.gdrive[a] = (float)c.g_drive[a];
+        d.ggrav[a] = (float)c.g_grav[a];
+    }
+    d.pitch = I.pitch;
+    d.qstride = I.qstride;
+    d.tile0 = I.tile0;
+    d.np = I.np;
+    d.maxk = I.maxk;
+    d.tau_inv = (float)(1.0 / c.tau);
+    d.keep = (float)(1.0 - 1.0 / c.tau);
+    d.fpref = (float)(1.0 - 1.0 / (2.0 * c.tau));
+    d.alpha = (float)c.alpha;
+    if (ctx->fp16) {
+        d.s_store = ldexpf(1.0f, c.fp16_scale_log2);
+        d.s_load = ldexpf(1.0f, -c.fp16_scale_log2);
+    } else {
+        d.s_store = d.s_load = 1.0f;
+    }
+    // bounce-back term 2 w_q (c_q . u_w) / cs^2 for every wall face
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < 2; ++f)
+            for (int q = 0; q < 19; ++q) {
+                double cu = 0, w = 0;
+                if (q < ctx->Q) {
+                    for (int e = 0; e < 3; ++e) {
+                        const int cq = ctx->Q == 9 ? d2q9_c(q, e) : d3q19_c(q, e);
+                        cu += cq * c.wall_u[a][f][e];
+                    }
+                    w = ctx->Q == 9 ? d2q9_w(q) : d3q19_w(q);
+                }
+                d.wterm[a][f][q] = (float)(2.0 * w * cu * 3.0);
+            }
+    d.f[0] = I.f[0].ptr;
+    d.f[1] = I.f[1].ptr;
+    d.prec = P<PRec>(I.prec);
+    d.list_cnt[0] = P<int>(I.lcnt[0]);
+    d.list_cnt[1] = P<int>(I.lcnt[1]);
+    d.list_ent[0] = P<uint32_t>(I.lent[0]);
+    d.list_ent[1] = P<uint32_t>(I.lent[1]);
+    d.partial = P<double>(I.partial);
+    d.X = P<double>(I.X);
+    d.U = P<double>(I.U);
+    d.W = P<double>(I.W);
+    d.Un = P<double>(I.Un);
+    d.Wn = P<double>(I.Wn);
+    d.theta = P<double>(I.theta);
+    d.A = P<double>(I.A);
+    d.R = P<double>(I.R);
+    d.ratio = P<double>(I.ratio);
+    d.count = P<int>(I.count);
+    d.Xk = P<double>(I.Xk);
+    d.Ubar = P<double>(I.Ubar);
+    d.Xf = P<float>(I.Xf);
+    d.rho_f = c.rho_f;
+    d.gmag = sqrt(c.g_grav[0] * c.g_grav[0] + c.g_grav[1] * c.g_grav[1] + c.g_grav[2] * c.g_grav[2]);
+    d.delta = c.delta;
+    d.eps_p = c.eps_p;
+    d.eps_w = c.eps_w;
+    d.K = c.K;
+    d.status = P<int>(ctx->d_status);
+    return d;
+}
+
+void invalidate_graphs(lbm_ctx* ctx) {
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->exec[i]) cudaGraphExecDestroy(ctx->exec[i]);
+        ctx->exec[i] = nullptr;
+        ctx->graph_ok[i] = false;
+    }
+}
+
+int upload_descs(lbm_ctx* ctx) {
+    std::vector<InstDesc> h;
+    for (auto& I : ctx->inst) h.push_back(make_desc(ctx, I));
+    int rc = dalloc(ctx, ctx->d_insts, sizeof(InstDesc) * h.size());
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->d_insts.ptr, h.data(), sizeof(InstDesc) * h.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+    // particle reference table for the per-particle kernels
+    std::vector<PartRef> refs;
+    for (int i = 0; i < (int)ctx->inst.size(); ++i)
+        for (int p = 0; p < ctx->inst[i].np; ++p) refs.push_back({i, p});
+    ctx->np_total = (int)refs.size();
+    rc = dalloc(ctx, ctx->d_refs, sizeof(PartRef) * std::max<size_t>(refs.size(), 1));
+    if (rc) return rc;
+    if (!refs.empty())
+        CK(cudaMemcpyAsync(ctx->d_refs.ptr, refs.data(), sizeof(PartRef) * refs.size(),
+                           cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));  // host vectors go out of scope
+    return LBM_OK;
+}
+
+// Re-publish every particle into the tile lists of the current parity.
+int republish(lbm_ctx* ctx) {
+    for (auto& I : ctx->inst) {
+        if (I.np == 0) continue;
+        CK(cudaMemsetAsync(I.lcnt[ctx->par].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
+    }
+    if (ctx->np_total > 0)
+        CK(launch_publish(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
+                          ctx->par, ctx->shape, ctx->st));
+    return LBM_OK;
+}
+
+// Tile grid, tile -> instance table, tile lists and partial slots for a shape.
+int configure_shape(lbm_ctx* ctx, const Shape& sh) {
+    ctx->shape = sh;
+    if (ctx->D == 2) ctx->shape.tz = 1;
+    const int T[3] = {32 * sh.vec, sh.ty, ctx->D == 2 ? 1 : sh.tz};
+    int tile0 = 0;
+    std::vector<uint16_t> tab;
+    for (int i = 0; i < (int)ctx->inst.size(); ++i) {
+        Instance& I = ctx->inst[i];
+        I.ntiles = 1;
+        for (int d = 0; d < 3; ++d) {
+            I.ntile[d] = (I.n[d] + T[d] - 1) / T[d];
+            I.ntiles *= I.ntile[d];
+        }
+        I.tile0 = tile0;
+        tile0 += I.ntiles;
+        tab.insert(tab.end(), (size_t)I.ntiles, (uint16_t)i);
+        I.maxk = max_slots(I, ctx->D, ctx->shape);
+        int rc;
+        for (int b = 0; b < 2; ++b) {
+            if ((rc = dalloc(ctx, I.lcnt[b], sizeof(int) * I.ntiles))) return rc;
+            if ((rc = dalloc(ctx, I.lent[b], sizeof(uint32_t) * (size_t)I.ntiles * LIST_CAP))) return rc;
+            CK(cudaMemsetAsync(I.lcnt[b].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
+        }
+        if ((rc = dalloc(ctx, I.partial, sizeof(double) * (size_t)std::max(I.cap, 1) * I.maxk * NPV)))
+            return rc;
+    }
+    ctx->ntiles = tile0;
+    int rc = dalloc(ctx, ctx->d_tile_inst, sizeof(uint16_t) * tab.size());
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->d_tile_inst.ptr, tab.data(), sizeof(uint16_t) * tab.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int occ = fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, ctx->shape);
+    ctx->grid = std::max(1, occ) * ctx->num_sms;
+    if ((rc = upload_descs(ctx))) return rc;
+    invalidate_graphs(ctx);
+    return republish(ctx);
+}
+
+Shape default_shape(int Q, int fp16) {
+    if (Q == 9) return fp16 ? Shape{8, 4, 1, 4, 0} : Shape{4, 4, 1, 4, 0};
+    return fp16 ? Shape{4, 2, 2, 4, 0} : Shape{2, 2, 2, 4, 0};
+}
+
+int enqueue_fluid(lbm_ctx* ctx, int commit) {
+    const Shape& sh = ctx->shape;
+    CK(launch_fluid(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), P<uint16_t>(ctx->d_tile_inst),
+                    ctx->ntiles, ctx->par, sh, commit, sh.persistent, ctx->grid,
+                    P<int>(ctx->d_tile_ctr), ctx->st));
+    return LBM_OK;
+}
+
+// One full time step on the stream (no synchronisation).
+int enqueue_step(lbm_ctx* ctx) {
+    int rc = enqueue_fluid(ctx, 1);
+    if (rc) return rc;
+    if (ctx->np_total > 0) {
+        const InstDesc* di = P<InstDesc>(ctx->d_insts);
+        const PartRef* dr = P<PartRef>(ctx->d_refs);
+        CK(launch_finalize(di, dr, ctx->np_total, ctx->D, ctx->st));
+        const int K = ctx->inst[0].cfg.K;
+        for (int k = 0; k < K; ++k)
+            CK(launch_substep(di, dr, ctx->np_total, ctx->D, k & 1, K, k == K - 1, ctx->par ^ 1,
+                              ctx->shape, ctx->st));
+    }
+    ctx->par ^= 1;
+    ctx->steps += 1;
+    return LBM_OK;
+}
+
+int check_ctx(lbm_ctx* ctx) {
+    if (!ctx) return LBM_ERR_INVALID;
+    if (ctx->failed) return LBM_ERR_STATE;
+    return LBM_OK;
+}
+
+int check_inst(lbm_ctx* ctx, int i) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (i < 0 || i >= (int)ctx->inst.size()) return set_err(ctx, LBM_ERR_INVALID, "bad instance index%s");
+    return LBM_OK;
+}
+
+int read_status(lbm_ctx* ctx) {
+    int st = 0;
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(&st, ctx->d_status.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == 0) return LBM_OK;
+    ctx->failed = true;
+    if (st & ST_DIVERGED) return set_err(ctx, LBM_ERR_DIVERGED, "the flow diverged (|u| >= 0.5 or non-finite)%s");
+    if (st & ST_PARTICLE) return set_err(ctx, LBM_ERR_PARTICLE, "a particle centre crossed a wall%s");
+    if (st & ST_DISPLACEMENT) return set_err(ctx, LBM_ERR_DIVERGED, "a particle moved faster than 0.5 per step%s");
+    return set_err(ctx, LBM_ERR_CAPACITY, "a tile overlaps more particles than its list holds%s");
+}
+
+void destroy_all(lbm_ctx* ctx) {
+    invalidate_graphs(ctx);
+    for (auto& I : ctx->inst) {
+        DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
+                          &I.partial, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
+                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf};
+        for (DevBuf* b : bufs) dfree(ctx, *b);
+    }
+    dfree(ctx, ctx->d_insts);
+    dfree(ctx, ctx->d_tile_inst);
+    dfree(ctx, ctx->d_tile_ctr);
+    dfree(ctx, ctx->d_status);
+    dfree(ctx, ctx->d_refs);
+}
+
+int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
+    DevBuf* v3[] = {&I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.Ubar};
+    int rc;
+    const size_t c = (size_t)std::max(cap, 1);
+    for (DevBuf* b : v3)
+        if ((rc = dalloc(ctx, *b, sizeof(double) * 3 * c))) return rc;
+    if ((rc = dalloc(ctx, I.R, sizeof(double) * c))) return rc;
+    if ((rc = dalloc(ctx, I.ratio, sizeof(double) * c))) return rc;
+    if ((rc = dalloc(ctx, I.count, sizeof(int) * c))) return rc;
+    if ((rc = dalloc(ctx, I.prec, sizeof(PRec) * c))) return rc;
+    if ((rc = dalloc(ctx, I.Xk, sizeof(double) * 6 * c))) return rc;
+    if ((rc = dalloc(ctx, I.Xf, sizeof(float) * 8 * c))) return rc;
+    if ((rc = dalloc(ctx, I.partial, sizeof(double) * c * std::max(I.maxk, 1) * NPV))) return rc;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(int s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_INVALID: return "invalid argument";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_OOM: return "out of device memory";
+        case LBM_ERR_DIVERGED: return "diverged";
+        case LBM_ERR_TIMEOUT: return "device wait timed out";
+        case LBM_ERR_STATE: return "context unusable";
+        case LBM_ERR_CAPACITY: return "tile list capacity exceeded";
+        case LBM_ERR_PARTICLE: return "particle left the box";
+        default: return "unknown status";
+    }
+}
+
+int lbm_config_default(lbm_config* cfg, int lattice, int nx, int ny, int nz) {
+    if (!cfg) return LBM_ERR_INVALID;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->lattice = lattice;
+    cfg->storage = LBM_FP32;
+    cfg->n[0] = nx;
+    cfg->n[1] = ny;
+    cfg->n[2] = lattice == LBM_D2Q9 ? 1 : nz;
+    for (int d = 0; d < 3; ++d) cfg->bc[d] = LBM_WALL;
+    if (lattice == LBM_D2Q9) cfg->bc[2] = LBM_PERIODIC;
+    cfg->tau = 1.0;
+    cfg->alpha = 1.0;
+    cfg->rho_f = 1.0;
+    cfg->delta = 1.0;
+    cfg->eps_p = 2.0;
+    cfg->eps_w = 1.0;
+    cfg->K = 1;
+    cfg->max_particles = 64;
+    cfg->max_radius = 16.0;
+    cfg->fp16_scale_log2 = 14;
+    return (lattice == LBM_D2Q9 || lattice == LBM_D3Q19) ? LBM_OK : LBM_ERR_INVALID;
+}
+
+int lbm_create_batch(const lbm_config* cfgs, int n, const lbm_allocator* alloc, void* stream,
+                     lbm_ctx** out) {
+    if (!cfgs || n < 1 || n > 65535 || !out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    char why[256];
+    for (int i = 0; i < n; ++i) {
+        if (!validate(&cfgs[i], why, sizeof why)) return LBM_ERR_INVALID;
+        if (cfgs[i].lattice != cfgs[0].lattice || cfgs[i].storage != cfgs[0].storage ||
+            cfgs[i].K != cfgs[0].K)
+            return LBM_ERR_INVALID;
+    }
+    lbm_ctx* ctx = new lbm_ctx();
+    ctx->Q = cfgs[0].lattice;
+    ctx->D = ctx->Q == 9 ? 2 : 3;
+    ctx->fp16 = cfgs[0].storage == LBM_FP16;
+    ctx->st = static_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) {
+        ctx->alloc = *alloc;
+        ctx->has_alloc = true;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    ctx->inst.resize(n);
+    ctx->shape = default_shape(ctx->Q, ctx->fp16);
+    if (n > 1) ctx->shape.persistent = 1;
+    const size_t ssz = ctx->fp16 ? 2 : 4;
+    int rc = LBM_OK;
+    for (int i = 0; i < n && rc == LBM_OK; ++i) {
+        Instance& I = ctx->inst[i];
+        I.cfg = cfgs[i];
+        for (int d = 0; d < 3; ++d) I.n[d] = cfgs[i].n[d];
+        if (ctx->D == 2) I.n[2] = 1;
+        I.pitch = (I.n[0] + 31) & ~31;
+        I.qstride = (long long)I.pitch * I.n[1] * I.n[2];
+        I.cap = cfgs[i].max_particles;
+        const size_t fb = ssz * (size_t)(ctx->Q - 1) * (size_t)I.qstride;
+        for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
+            rc = dalloc(ctx, I.f[b], fb);
+            if (rc == LBM_OK && cudaMemsetAsync(I.f[b].ptr, 0, fb, ctx->st) != cudaSuccess)
+                rc = LBM_ERR_CUDA;
+        }
+        if (rc == LBM_OK) rc = alloc_particles(ctx, I, I.cap);
+    }
+    if (rc == LBM_OK) rc = dalloc(ctx, ctx->d_tile_ctr, sizeof(int) * 2);
+    if (rc == LBM_OK) rc = dalloc(ctx, ctx->d_status, sizeof(int) * 4);
+    if (rc == LBM_OK) {
+        cudaMemsetAsync(ctx->d_tile_ctr.ptr, 0, sizeof(int) * 2, ctx->st);
+        cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * 4, ctx->st);
+        rc = configure_shape(ctx, ctx->shape);
+    }
+    if (rc == LBM_OK && cudaStreamSynchronize(ctx->st) != cudaSuccess) rc = LBM_ERR_CUDA;
+    if (rc != LBM_OK) {
+        destroy_all(ctx);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_config* cfg, const lbm_allocator* alloc, void* stream, lbm_ctx** out) {
+    return lbm_create_batch(cfg, 1, alloc, stream, out);
+}
+
+int lbm_num_instances(const lbm_ctx* ctx) { return ctx ? (int)ctx->inst.size() : 0; }
+
+int lbm_num_particles(const lbm_ctx* ctx, int i) {
+    if (!ctx || i < 0 || i >= (int)ctx->inst.size()) return -1;
+    return ctx->inst[i].np;
+}
+
+int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const double* radius,
+                      const double* ratio, const double* vel, const double* omega) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!pos || !radius || !ratio)))
+        return set_err(ctx, LBM_ERR_INVALID, "bad particle arrays%s");
+    if (n == 0) return LBM_OK;
+    Instance& I = ctx->inst[i];
+    const int D = ctx->D;
+    if (I.np + n > I.cap) return set_err(ctx, LBM_ERR_INVALID, "max_particles exceeded%s");
+    for (int k = 0; k < n; ++k) {
+        if (!(radius[k] >= 2.0) || radius[k] > I.cfg.max_radius)
+            return set_err(ctx, LBM_ERR_INVALID, "radius must lie in [2, max_radius]%s");
+        if (!(ratio[k] > 0.0)) return set_err(ctx, LBM_ERR_INVALID, "density ratio must be positive%s");
+        for (int d = 0; d < D; ++d) {
+            const double x = pos[k * D + d];
+            if (!(x == x)) return set_err(ctx, LBM_ERR_INVALID, "non-finite position%s");
+            if (I.cfg.bc[d] == LBM_WALL && (x < 0.0 || x > I.n[d] - 1))
+                return set_err(ctx, LBM_ERR_INVALID, "particle centre outside the box%s");
+            if (I.cfg.bc[d] == LBM_PERIODIC && (x < 0.0 || x >= I.n[d] ||
+                                                 radius[k] >= 0.25 * I.n[d]))
+                return set_err(ctx, LBM_ERR_INVALID,
+                               "periodic axis: need 0 <= x < n and radius < n/4%s");
+        }
+    }
+    // host staging, FP64 [n][3]
+    std::vector<double> X(3 * n, 0.0), U(3 * n, 0.0), W(3 * n, 0.0), Z(3 * n, 0.0);
+    for (int k = 0; k < n; ++k)
+        for (int d = 0; d < D; ++d) {
+            X[3 * k + d] = pos[k * D + d];
+            if (vel) U[3 * k + d] = vel[k * D + d];
+        }
+    if (omega) {
+        for (int k = 0; k < n; ++k) {
+            if (D == 2) W[3 * k + 2] = omega[k];
+            else
+                for (int d = 0; d < 3; ++d) W[3 * k + d] = omega[3 * k + d];
+        }
+    }
+    const size_t o3 = sizeof(double) * 3 * I.np, b3 = sizeof(double) * 3 * n;
+    auto up = [&](DevBuf& b, const std::vector<double>& v) {
+        return cudaMemcpyAsync(static_cast<char*>(b.ptr) + o3, v.data(), b3, cudaMemcpyHostToDevice,
+                               ctx->st);
+    };
+    CK(up(I.X, X));
+    CK(up(I.U, U));
+    CK(up(I.W, W));
+    CK(up(I.Un, U));
+    CK(up(I.Wn, W));
+    CK(up(I.theta, Z));
+    CK(up(I.A, Z));
+    CK(cudaMemcpyAsync(P<double>(I.R) + I.np, radius, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(P<double>(I.ratio) + I.np, ratio, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(P<int>(I.count) + I.np, 0, sizeof(int) * n, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    I.np += n;
+    I.hR.insert(I.hR.end(), radius, radius + n);
+    if ((rc = upload_descs(ctx))) return rc;
+    invalidate_graphs(ctx);
+    return republish(ctx);
+}
+
+int lbm_step(lbm_ctx* ctx, int nsteps) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (nsteps < 0) return set_err(ctx, LBM_ERR_INVALID, "negative step count%s");
+    const int G = ctx->graph_steps;
+    while (nsteps > 0) {
+        if (G > 0 && nsteps >= G) {
+            const int p = ctx->par;
+            if (!ctx->graph_ok[p]) {
+                cudaGraph_t g = nullptr;
+                const long long s0 = ctx->steps;
+                CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+                int err = LBM_OK;
+                for (int k = 0; k < G && err == LBM_OK; ++k) err = enqueue_step(ctx);
+                cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+                ctx->steps = s0;
+                ctx->par = p;
+                if (err) return err;
+                if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture");
+                e = cudaGraphInstantiate(&ctx->exec[p], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
+                ctx->graph_ok[p] = true;
+            }
+            CK(cudaGraphLaunch(ctx->exec[p], ctx->st));
+            ctx->steps += G;  // G is even: the parity returns to p
+            nsteps -= G;
+        } else {
+            if ((rc = enqueue_step(ctx))) return rc;
+            nsteps -= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* ctx) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    return read_status(ctx);
+}
+
+int lbm_fluid_step_only(lbm_ctx* ctx) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    return enqueue_fluid(ctx, 0);
+}
+
+int lbm_get_fields(lbm_ctx* ctx, int i, float* u, float* p, int* owner, int on_device) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    Instance& I = ctx->inst[i];
+    const long long N = (long long)I.n[0] * I.n[1] * I.n[2];
+    if (on_device) {
+        CK(launch_fields(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), i, N, ctx->par, ctx->shape, u,
+                         p, owner, ctx->st));
+        return LBM_OK;
+    }
+    DevBuf du, dp, dow;
+    if ((u && (rc = dalloc(ctx, du, sizeof(float) * ctx->D * N))) ||
+        (p && (rc = dalloc(ctx, dp, sizeof(float) * N))) ||
+        (owner && (rc = dalloc(ctx, dow, sizeof(int) * N)))) {
+        dfree(ctx, du); dfree(ctx, dp); dfree(ctx, dow);
+        return rc;
+    }
+    cudaError_t e = launch_fields(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), i, N, ctx->par,
+                                  ctx->shape, P<float>(du), P<float>(dp), P<int>(dow), ctx->st);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du.ptr, sizeof(float) * ctx->D * N, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess && p) e = cudaMemcpyAsync(p, dp.ptr, sizeof(float) * N, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess && owner) e = cudaMemcpyAsync(owner, dow.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    dfree(ctx, du); dfree(ctx, dp); dfree(ctx, dow);
+    return cuda_err(ctx, e, "lbm_get_fields");
+}
+
+int lbm_get_particles(lbm_ctx* ctx, int i, double* pos, double* vel, double* omega, double* theta,
+                      double* accel, int* count) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    Instance& I = ctx->inst[i];
+    const int n = I.np, D = ctx->D;
+    if (n == 0) return LBM_OK;
+    std::vector<double> X(3 * n), U(3 * n), W(3 * n), T(3 * n), A(3 * n);
+    std::vector<int> C(n);
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(X.data(), I.X.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(U.data(), I.U.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(W.data(), I.W.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(T.data(), I.theta.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(A.data(), I.A.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(C.data(), I.count.ptr, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n; ++k) {
+        for (int d = 0; d < D; ++d) {
+            if (pos) pos[k * D + d] = X[3 * k + d];
+            if (vel) vel[k * D + d] = U[3 * k + d];
+            if (accel) accel[k * D + d] = A[3 * k + d];
+        }
+        if (D == 2) {
+            if (omega) omega[k] = W[3 * k + 2];
+            if (theta) theta[k] = T[3 * k + 2];
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                if (omega) omega[3 * k + d] = W[3 * k + d];
+                if (theta) theta[3 * k + d] = T[3 * k + d];
+            }
+        }
+        if (count) count[k] = C[k];
+    }
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* ctx, int i, const float* f, int on_device) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    if (!f) return set_err(ctx, LBM_ERR_INVALID, "null population array%s");
+    Instance& I = ctx->inst[i];
+    const long long N = (long long)I.n[0] * I.n[1] * I.n[2];
+    const float* src = f;
+    DevBuf tmp;
+    if (!on_device) {
+        if ((rc = dalloc(ctx, tmp, sizeof(float) * ctx->Q * N))) return rc;
+        CK(cudaMemcpyAsync(tmp.ptr, f, sizeof(float) * ctx->Q * N, cudaMemcpyHostToDevice, ctx->st));
+        src = P<float>(tmp);
+    }
+    cudaError_t e = launch_pack(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), i, N, ctx->par, src, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    dfree(ctx, tmp);
+    return cuda_err(ctx, e, "lbm_set_populations");
+}
+
+int lbm_get_populations(lbm_ctx* ctx, int i, float* f, int on_device) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    if (!f) return set_err(ctx, LBM_ERR_INVALID, "null population array%s");
+    Instance& I = ctx->inst[i];
+    const long long N = (long long)I.n[0] * I.n[1] * I.n[2];
+    if (on_device) {
+        CK(launch_unpack(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), i, N, ctx->par, f, ctx->st));
+        return LBM_OK;
+    }
+    DevBuf tmp;
+    if ((rc = dalloc(ctx, tmp, sizeof(float) * ctx->Q * N))) return rc;
+    cudaError_t e = launch_unpack(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), i, N, ctx->par,
+                                  P<float>(tmp), ctx->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, tmp.ptr, sizeof(float) * ctx->Q * N, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    dfree(ctx, tmp);
+    return cuda_err(ctx, e, "lbm_get_populations");
+}
+
+// State blob: header, then per instance the stored populations of the current
+// parity followed by the FP64 particle arrays.
+int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!bytes) return LBM_ERR_INVALID;
+    const size_t ssz = ctx->fp16 ? 2 : 4;
+    size_t total = 4 * sizeof(long long);
+    for (auto& I : ctx->inst)
+        total += sizeof(long long) + ssz * (ctx->Q - 1) * I.qstride +
+                 (size_t)I.np * (sizeof(double) * (7 * 3 + 2) + sizeof(int));
+    if (!buf) {
+        *bytes = total;
+        return LBM_OK;
+    }
+    if (*bytes < total) return set_err(ctx, LBM_ERR_INVALID, "state buffer too small%s");
+    CK(cudaStreamSynchronize(ctx->st));
+    char* w = static_cast<char*>(buf);
+    long long hdr[4] = {0x4c424d50454e31LL, (long long)ctx->inst.size(), ctx->steps, ctx->Q};
+    memcpy(w, hdr, sizeof hdr);
+    w += sizeof hdr;
+    for (auto& I : ctx->inst) {
+        long long np = I.np;
+        memcpy(w, &np, sizeof np);
+        w += sizeof np;
+        const size_t fb = ssz * (ctx->Q - 1) * I.qstride;
+        CK(cudaMemcpy(w, I.f[ctx->par].ptr, fb, cudaMemcpyDeviceToHost));
+        w += fb;
+        DevBuf* v3[] = {&I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A};
+        for (DevBuf* b : v3) {
+            CK(cudaMemcpy(w, b->ptr, sizeof(double) * 3 * I.np, cudaMemcpyDeviceToHost));
+            w += sizeof(double) * 3 * I.np;
+        }
+        CK(cudaMemcpy(w, I.R.ptr, sizeof(double) * I.np, cudaMemcpyDeviceToHost));
+        w += sizeof(double) * I.np;
+        CK(cudaMemcpy(w, I.ratio.ptr, sizeof(double) * I.np, cudaMemcpyDeviceToHost));
+        w += sizeof(double) * I.np;
+        CK(cudaMemcpy(w, I.count.ptr, sizeof(int) * I.np, cudaMemcpyDeviceToHost));
+        w += sizeof(int) * I.np;
+    }
+    *bytes = total;
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!buf || bytes < 4 * sizeof(long long)) return LBM_ERR_INVALID;
+    const char* r = static_cast<const char*>(buf);
+    long long hdr[4];
+    memcpy(hdr, r, sizeof hdr);
+    r += sizeof hdr;
+    if (hdr[0] != 0x4c424d50454e31LL || hdr[1] != (long long)ctx->inst.size() || hdr[3] != ctx->Q)
+        return set_err(ctx, LBM_ERR_INVALID, "state blob does not match this context%s");
+    const size_t ssz = ctx->fp16 ? 2 : 4;
+    size_t need = sizeof hdr;
+    {
+        const char* q = r;
+        for (auto& I : ctx->inst) {
+            if ((size_t)(q - static_cast<const char*>(buf)) + sizeof(long long) > bytes) return LBM_ERR_INVALID;
+            long long np;
+            memcpy(&np, q, sizeof np);
+            if (np < 0 || np > I.cap) return set_err(ctx, LBM_ERR_INVALID, "particle count exceeds capacity%s");
+            const size_t add = sizeof(long long) + ssz * (ctx->Q - 1) * I.qstride +
+                               (size_t)np * (sizeof(double) * 23 + sizeof(int));
+            need += add;
+            q += add;
+        }
+    }
+    if (need > bytes) return set_err(ctx, LBM_ERR_INVALID, "state blob truncated%s");
+    CK(cudaStreamSynchronize(ctx->st));
+    for (auto& I : ctx->inst) {
+        long long np;
+        memcpy(&np, r, sizeof np);
+        r += sizeof np;
+        const size_t fb = ssz * (ctx->Q - 1) * I.qstride;
+        CK(cudaMemcpy(I.f[ctx->par].ptr, r, fb, cudaMemcpyHostToDevice));
+        r += fb;
+        I.np = (int)np;
+        DevBuf* v3[] = {&I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A};
+        for (DevBuf* b : v3) {
+            CK(cudaMemcpy(b->ptr, r, sizeof(double) * 3 * I.np, cudaMemcpyHostToDevice));
+            r += sizeof(double) * 3 * I.np;
+        }
+        I.hR.assign(reinterpret_cast<const double*>(r), reinterpret_cast<const double*>(r) + I.np);
+        CK(cudaMemcpy(I.R.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
+        r += sizeof(double) * I.np;
+        CK(cudaMemcpy(I.ratio.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
+        r += sizeof(double) * I.np;
+        CK(cudaMemcpy(I.count.ptr, r, sizeof(int) * I.np, cudaMemcpyHostToDevice));
+        r += sizeof(int) * I.np;
+    }
+    ctx->steps = hdr[2];
+    if ((rc = upload_descs(ctx))) return rc;
+    invalidate_graphs(ctx);
+    return republish(ctx);
+}
+
+int lbm_set_graphs(lbm_ctx* ctx, int steps_per_graph) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (steps_per_graph < 0 || (steps_per_graph & 1))
+        return set_err(ctx, LBM_ERR_INVALID, "steps_per_graph must be 0 or a positive even number%s");
+    ctx->graph_steps = steps_per_graph;
+    invalidate_graphs(ctx);
+    return LBM_OK;
+}
+
+int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps) {
+    if (!ctx) return LBM_ERR_INVALID;
+    if (vec) *vec = ctx->shape.vec;
+    if (tile_rows) *tile_rows = ctx->shape.ty * ctx->shape.tz;
+    if (warps) *warps = ctx->shape.warps;
+    return LBM_OK;
+}
+
+static bool shape_ok(const lbm_ctx* ctx, int vec) {
+    return ctx->fp16 ? (vec == 2 || vec == 4 || vec == 8) : (vec == 1 || vec == 2 || vec == 4);
+}
+
+int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!shape_ok(ctx, vec) || tile_rows < 1 || tile_rows > 64 || warps < 1 || warps > 8)
+        return set_err(ctx, LBM_ERR_INVALID, "unsupported kernel shape%s");
+    Shape s = ctx->shape;
+    s.vec = vec;
+    s.warps = warps;
+    if (ctx->D == 2) {
+        s.ty = tile_rows;
+        s.tz = 1;
+    } else {
+        int tz = 1;
+        while (tz * tz < tile_rows) tz *= 2;
+        if (tile_rows % tz) return set_err(ctx, LBM_ERR_INVALID, "3D tile rows must factor as ty*tz%s");
+        s.tz = tz;
+        s.ty = tile_rows / tz;
+    }
+    return configure_shape(ctx, s);
+}
+
+int lbm_autotune(lbm_ctx* ctx, int reps) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (reps < 1) reps = 5;
+    std::vector<Shape> cand;
+    const int vecs32[] = {1, 2, 4}, vecs16[] = {2, 4, 8};
+    const int* vecs = ctx->fp16 ? vecs16 : vecs32;
+    for (int vi = 0; vi < 3; ++vi)
+        for (int rows : {2, 4, 8})
+            for (int warps : {2, 4, 8})
+                for (int pers : {0, 1}) {
+                    if (warps > rows) continue;
+                    Shape s{vecs[vi], rows, 1, warps, pers};
+                    if (ctx->D == 3) {
+                        s.tz = rows >= 4 ? 2 : 1;
+                        s.ty = rows / s.tz;
+                    }
+                    cand.push_back(s);
+                }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Shape bests = ctx->shape;
+    for (const Shape& s : cand) {
+        if ((rc = configure_shape(ctx, s))) break;
+        if (fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, ctx->shape) < 1) continue;
+        for (int w = 0; w < 2; ++w)
+            if ((rc = enqueue_fluid(ctx, 0))) break;
+        if (rc) break;
+        cudaEventRecord(e0, ctx->st);
+        for (int k = 0; k < reps && rc == LBM_OK; ++k) rc = enqueue_fluid(ctx, 0);
+        cudaEventRecord(e1, ctx->st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = LBM_ERR_CUDA;
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bests = ctx->shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = configure_shape(ctx, bests);
+    return rc ? rc : rc2;
+}
+
+int lbm_launches_per_step(const lbm_ctx* ctx) {
+    if (!ctx) return 0;
+    return 1 + (ctx->np_total > 0 ? 1 + ctx->inst[0].cfg.K : 0);
+}
+
+long long lbm_steps_done(const lbm_ctx* ctx) { return ctx ? ctx->steps : 0; }
+
+long long lbm_total_nodes(const lbm_ctx* ctx) {
+    if (!ctx) return 0;
+    long long n = 0;
+    for (auto& I : ctx->inst) n += (long long)I.n[0] * I.n[1] * I.n[2];
+    return n;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    destroy_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Internal device-side definitions of lbmpen (not part of the C ABI).
+//
+// Layout in HBM, per instance:
+//   populations  f[2][QS][nz][ny][pitch]  (ping-pong; QS = Q - 1 because the
+//                rest population is never read back, see lbmpen.h), FP32 or
+//                FP16 (scaled by 2^k); pitch = nx rounded up to 32 elements
+//                so every row starts on a 128-byte boundary;
+//   particles    FP64 state arrays [np][3] plus one PRec per particle that
+//                the fluid kernel reads (centre, radius, solid acceleration);
+//   tile lists   list_cnt[2][ntiles], list_ent[2][ntiles][cap]: for each
+//                tile the particles whose bounding box overlaps it, built by
+//                the particle kernel for the next step (no per-node mask);
+//   partials     partial[np][maxk][NPV] FP64: per particle and per tile of its
+//                bounding box, the sums of Eq. 22 over that tile.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmpen {
+
+// ---------------------------------------------------------------- lattices --
+// D2Q9 in the paper's Fig. 1 numbering and D3Q19; q = 0 is the rest velocity.
+__host__ __device__ constexpr int d2q9_c(int q, int d) {
+    return d == 0 ? (q == 1 || q == 5 || q == 8 ? 1 : (q == 3 || q == 6 || q == 7 ? -1 : 0))
+         : d == 1 ? (q == 2 || q == 5 || q == 6 ? 1 : (q == 4 || q == 7 || q == 8 ? -1 : 0))
+                  : 0;
+}
+__host__ __device__ constexpr int d2q9_opp(int q) {
+    return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 5 + 2) % 4) + 5);
+}
+__host__ __device__ constexpr float d2q9_w(int q) {
+    return q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// D3Q19: 1..6 axes (+x,-x,+y,-y,+z,-z), 7..18 edges in opposite pairs
+__host__ __device__ constexpr int d3q19_c(int q, int d) {
+    // rows: x, y, z components for q = 0..18
+    return d == 0 ? (q == 1 || q == 7 || q == 9 || q == 11 || q == 13 ? 1
+                     : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14 ? -1 : 0))
+         : d == 1 ? (q == 3 || q == 7 || q == 10 || q == 15 || q == 17 ? 1
+                     : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18 ? -1 : 0))
+                  : (q == 5 || q == 11 || q == 14 || q == 15 || q == 18 ? 1
+                     : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17 ? -1 : 0));
+}
+__host__ __device__ constexpr int d3q19_opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr float d3q19_w(int q) {
+    return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+template <int Q> struct Lat;
+template <> struct Lat<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int c(int q, int d) { return d2q9_c(q, d); }
+    __host__ __device__ static constexpr int opp(int q) { return d2q9_opp(q); }
+    __host__ __device__ static constexpr float w(int q) { return d2q9_w(q); }
+};
+template <> struct Lat<19> {
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int c(int q, int d) { return d3q19_c(q, d); }
+    __host__ __device__ static constexpr int opp(int q) { return d3q19_opp(q); }
+    __host__ __device__ static constexpr float w(int q) { return d3q19_w(q); }
+};
+
+// ------------------------------------------------------------- descriptors --
+// Number of FP64 values per (particle, tile) partial:
+//   0 count, 1-3 sum d, 4-9 sum d_i d_j (xx, yy, zz, xy, xz, yz),
+//   10-12 sum u, 13-15 sum d x u;  d = node - floor(X) (integer offsets).
+constexpr int NPV = 16;
+constexpr int LIST_CAP = 64;   // particles listed per tile (overflow -> LBM_ERR_CAPACITY)
+constexpr int KBITS = 10;      // list entry = particle << KBITS | slot
+constexpr int MAXK = 1 << KBITS;
+
+// Status word bits (device), mapped to lbm_status on the host.
+enum { ST_DIVERGED = 1, ST_CAPACITY = 2, ST_PARTICLE = 4, ST_DISPLACEMENT = 8 };
+
+// Particle record read by the fluid kernel; written by the particle kernel
+// for the next step.
+struct __align__(16) PRec {
+    double X[3];     // centre X^n (FP64, exact indicator test)
+    double R2;       // R * R
+    int ref[3];      // floor(X) per axis
+    int ntiles;      // tiles of the bounding box (slots written this step)
+    float frac[3];   // X - floor(X) as float (filter test)
+    float R2lo, R2hi;  // float thresholds: d2 < R2lo inside, d2 > R2hi outside
+    float a[3];      // solid-node acceleration (1 - rho_f/rho_s) g + A_i
+    int pad;
+};
+
+struct InstDesc {
+    int n[3];
+    int pitch;
+    long long qstride;        // elements per stored population
+    int periodic[3];
+    int ntile[3];             // tiles per axis
+    int tile0;                // first global tile of this instance
+    int np;                   // particles
+    int maxk;                 // partial slots per particle
+    int part0;                // global index of particle 0 (batched arrays)
+    float tau_inv, keep;      // 1/tau and 1 - 1/tau
+    float fpref;              // 1 - 1/(2 tau)
+    float alpha;
+    float gdrive[3];
+    float ggrav[3];
+    float s_store, s_load;    // FP16 storage scale 2^k and 2^-k (1 for FP32)
+    float wterm[3][2][19];    // bounce-back term 2 w_q (c_q . u_wall) / cs^2 per face
+    void* f[2];
+    PRec* prec;               // [np]
+    int* list_cnt[2];         // [ntiles]
+    uint32_t* list_ent[2];    // [ntiles][LIST_CAP]
+    double* partial;          // [np][maxk][NPV]
+    // particle state (FP64), [np][3] unless noted
+    double* X;
+    double* U;                // U^{n-1} entering the step, U^n after it
+    double* W;
+    double* Un;               // U^n of the current step (finalised)
+    double* Wn;
+    double* theta;
+    double* A;
+    double* R;                // [np]
+    double* ratio;            // [np] rho_s / rho_f
+    int* count;               // [np]
+    double* Xk;               // [2][np][3] Algorithm-1 sub-step positions
+    double* Ubar;             // [np][3]
+    float* Xf;                // [np][4] float copy of X^{k} for the pair filter
+    double rho_f;
+    double gmag;              // |g_grav|
+    double delta, eps_p, eps_w;
+    int K;
+    int* status;
+};
+
+// Kernel shape of the fused fluid kernel: a tile is (32 * vec) x rows_y x rows_z
+// nodes; each warp handles whole x-rows of the tile.
+struct Shape {
+    int vec;     // nodes per thread along x (vector width)
+    int ty, tz;  // tile rows along y and z
+    int warps;   // warps per block
+    int persistent;  // 1: grid-stride blocks pulling tiles from a work counter
+};
+
+// Particle index -> (instance, local index) for the per-particle kernels.
+struct PartRef {
+    int inst;
+    int p;
+};
+
+__host__ __device__ inline int tile_w(const Shape& s) { return 32 * s.vec; }
+
+}  // namespace lbmpen

@@ -1,0 +1,62 @@
+"""Helpers that run the same seeded workload through the CUDA library and the oracle."""
+import numpy as np
+
+import oracle
+from paper_2511_01629_gb300 import lbm
+
+
+def oracle_config(w):
+    return oracle.make_config(D=w.D, n=w.n, periodic=w.periodic, wall_u=w.wall_u, tau=w.tau,
+                              alpha=w.alpha, g_drive=w.g_drive, g_grav=w.g_grav, delta=w.delta,
+                              eps_p=w.eps_p, eps_w=w.eps_w, K=w.K)
+
+
+def make_pair(w, storage=lbm.LBM_FP32, f0=None, graphs=0, shape=None):
+    """(gpu context, oracle sim) for workload w, optionally from populations f0 [Q, ...]."""
+    sim = lbm.from_workloads([w], storage)
+    sim.set_graphs(graphs)
+    if shape is not None:
+        sim.set_kernel_shape(*shape)
+    ref = oracle.Sim(oracle_config(w))
+    if f0 is not None:
+        f32 = np.asarray(f0, np.float32)
+        sim.set_populations(f32)
+        ref.set_f(f32.astype(np.float64))
+    if w.num_particles:
+        ref.add_particles(w.pos, w.radius, w.ratio)
+    return sim, ref
+
+
+def random_state(seed, Q, shape, scale=1e-3):
+    """Random post-collision populations with f_0 = 0 (f_0 is not stored on the GPU)."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(-scale, scale, (Q,) + tuple(shape)).astype(np.float32)
+    f[0] = 0
+    return f
+
+
+def compare_fields(sim, ref, i=0):
+    u, p, own = sim.fields(i)
+    ur, pr, ownr = ref.fields()
+    uref = max(np.abs(ur).max(), 1e-30)
+    return {
+        "du": float(np.abs(u - ur).max() / uref),
+        "dp": float(np.abs(p - pr).max() / max(np.abs(pr).max(), 1e-30)),
+        "owner_equal": bool(np.array_equal(own, ownr)),
+        "owner_diff": int((own != ownr).sum()),
+        "uref": float(uref),
+    }
+
+
+def compare_particles(sim, ref, i=0):
+    a = sim.particles(i)
+    b = ref.particles()
+    D = sim.D
+    out = {}
+    for k in ("X", "U", "A"):
+        out["d" + k] = float(np.abs(a[k] - b[k][:, :D]).max()) if len(a[k]) else 0.0
+    wcol = [2] if D == 2 else [0, 1, 2]
+    out["dW"] = float(np.abs(a["W"] - b["W"][:, wcol]).max()) if len(a["W"]) else 0.0
+    out["count_equal"] = bool(np.array_equal(a["count"], b["count"]))
+    out["Uscale"] = float(np.abs(b["U"]).max()) if len(a["U"]) else 0.0
+    return out

@@ -1,0 +1,194 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances: the fused kernel computes in FP32, the oracle in FP64.  One step
+from a random state agrees to a few FP32 ulps of the population scale; over
+many steps the velocity error stays below 1e-6 of the velocity scale U_ref =
+max |u_oracle|.  The solid indicator and the integer parts of the
+projection are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_01629_gb300 import lbm
+from paper_2511_01629_gb300 import workloads as W
+
+from harness import compare_fields, compare_particles, make_pair, random_state
+
+gpu = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu_setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    lbm.build()
+    yield
+
+
+CASES_2D = [
+    # (n, periodic, nparticles)
+    ((37, 23, 1), (1, 0, 1), 2),      # ragged, one tile wide
+    ((130, 17, 1), (0, 0, 1), 3),     # two tiles with a 2-node tail
+    ((64, 40, 1), (1, 1, 1), 3),      # fully periodic
+    ((200, 33, 1), (0, 1, 1), 4),     # walls in x, periodic in y
+]
+
+
+@gpu
+@pytest.mark.parametrize("case", CASES_2D)
+@pytest.mark.parametrize("vec", [1, 2, 4])
+def test_one_step_from_random_state_d2q9(case, vec):
+    n, per, npart = case
+    w = W.random_small(5 + vec, D=2, n=n, periodic=per, nparticles=npart, rlo=2.5, rhi=6.0,
+                       tau=0.8, g_grav=(2e-5, -1e-4, 0), g_drive=(1e-5, 0, 0))
+    f0 = random_state(vec, 9, (n[1], n[0]))
+    sim, ref = make_pair(w, f0=f0, shape=(vec, 4, 4))
+    sim.step(1)
+    ref.step(1)
+    sim.sync()
+    fg = sim.get_populations()
+    fr = ref.get_f()
+    scale = np.abs(fr[1:]).max()
+    assert np.abs(fg[1:] - fr[1:]).max() < 2e-6 * scale
+    cf = compare_fields(sim, ref)
+    assert cf["owner_equal"], cf
+    assert cf["du"] < 2e-6, cf
+    cp = compare_particles(sim, ref)
+    assert cp["count_equal"], cp
+    assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-12), cp
+    assert cp["dX"] < 1e-9, cp
+
+
+@gpu
+@pytest.mark.parametrize("n,per", [((20, 18, 14), (1, 0, 1)), ((45, 12, 10), (0, 0, 0)),
+                                   ((16, 16, 16), (1, 1, 1))])
+@pytest.mark.parametrize("vec", [1, 2, 4])
+def test_one_step_from_random_state_d3q19(n, per, vec):
+    w = W.random_small(11 + vec, D=3, n=n, periodic=per, nparticles=2, rlo=2.5, rhi=4.0, tau=0.9,
+                       g_grav=(0, 2e-5, -1e-4))
+    f0 = random_state(vec + 3, 19, (n[2], n[1], n[0]))
+    sim, ref = make_pair(w, f0=f0, shape=(vec, 4, 4))
+    sim.step(1)
+    ref.step(1)
+    sim.sync()
+    fg = sim.get_populations()
+    fr = ref.get_f()
+    scale = np.abs(fr[1:]).max()
+    assert np.abs(fg[1:] - fr[1:]).max() < 2e-6 * scale
+    cf = compare_fields(sim, ref)
+    assert cf["owner_equal"], cf
+    assert cf["du"] < 2e-6, cf
+    cp = compare_particles(sim, ref)
+    assert cp["count_equal"], cp
+    assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-12), cp
+
+
+@gpu
+def test_poiseuille_disk_2000_steps():
+    """100x200 channel, tau 0.8, drive 1e-6, neutrally buoyant disk R = 8:
+    velocity within 1e-6 of U_ref after 2000 steps (graph-replayed steps)."""
+    w = W.poiseuille_disk(seed=0)
+    sim, ref = make_pair(w, graphs=16)
+    sim.step(w.steps)
+    ref.step(w.steps)
+    sim.sync()
+    cf = compare_fields(sim, ref)
+    cp = compare_particles(sim, ref)
+    assert cf["owner_equal"], cf
+    assert cf["du"] < 1e-6, cf
+    assert cp["dX"] < 1e-6, cp
+    assert cp["dU"] < 1e-6 * cf["uref"], cp
+
+
+@gpu
+def test_moving_wall_couette():
+    """Moving-wall bounce-back (walls at +-U_w/2) against the oracle."""
+    wall = np.zeros((3, 2, 3))
+    wall[1, 0, 0], wall[1, 1, 0] = -0.01, 0.01
+    w = W.random_small(2, D=2, n=(50, 40, 1), periodic=(1, 0, 1), nparticles=1, rlo=5, rhi=6,
+                       tau=1.0, g_grav=(0, 0, 0))
+    w.wall_u = wall.tolist()
+    w.ratio = [1.0]
+    sim, ref = make_pair(w)
+    sim.step(300)
+    ref.step(300)
+    sim.sync()
+    cf = compare_fields(sim, ref)
+    assert cf["owner_equal"] and cf["du"] < 1e-6, cf
+
+
+@gpu
+def test_determinism_bitwise():
+    w = W.random_small(9, D=2, n=(150, 90, 1), periodic=(0, 0, 1), nparticles=6, rlo=3, rhi=8,
+                       tau=1.0, g_grav=(0, -1e-4, 0))
+    outs = []
+    for _ in range(2):
+        sim = lbm.from_workloads([w])
+        sim.step(40)
+        sim.sync()
+        outs.append((sim.get_populations(), sim.particles()))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in ("X", "U", "W", "A"):
+        assert np.array_equal(outs[0][1][k], outs[1][1][k])
+
+
+@gpu
+def test_batched_instances_match_single():
+    ws = [W.random_small(20 + i, D=2, n=(40 + 17 * i, 30 + 5 * i, 1), periodic=(0, 0, 1),
+                         nparticles=1 + i, rlo=3, rhi=6, tau=1.0, g_grav=(0, -1e-4, 0))
+          for i in range(4)]
+    batch = lbm.from_workloads(ws)
+    batch.step(30)
+    batch.sync()
+    for i, w in enumerate(ws):
+        single = lbm.from_workloads([w])
+        single.step(30)
+        single.sync()
+        assert np.array_equal(batch.get_populations(i), single.get_populations())
+        for k in ("X", "U"):
+            assert np.array_equal(batch.particles(i)[k], single.particles()[k])
+        single.close()
+
+
+@gpu
+def test_save_load_roundtrip():
+    w = W.random_small(4, D=2, n=(60, 50, 1), periodic=(1, 0, 1), nparticles=3, rlo=3, rhi=5,
+                       tau=0.9, g_grav=(0, -1e-4, 0))
+    sim = lbm.from_workloads([w])
+    sim.step(10)
+    blob = sim.save_state()
+    sim.step(15)
+    sim.sync()
+    f_a, p_a = sim.get_populations(), sim.particles()
+    sim.load_state(blob)
+    sim.step(15)
+    sim.sync()
+    assert np.array_equal(sim.get_populations(), f_a)
+    assert np.array_equal(sim.particles()["X"], p_a["X"])
+
+
+@gpu
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(lbm.LBMError):
+        lbm.LBM(lbm.make_config(lbm.LBM_D2Q9, (10, 10, 1), tau=0.4))
+    sim = lbm.LBM(lbm.make_config(lbm.LBM_D2Q9, (32, 32, 1), max_particles=2))
+    with pytest.raises(lbm.LBMError):
+        sim.add_particles(0, [[40.0, 5.0]], [3.0], [1.5])  # outside the box
+    with pytest.raises(lbm.LBMError):
+        sim.add_particles(0, [[10.0, 10.0]], [1.0], [1.5])  # radius < 2
+    with pytest.raises(lbm.LBMError):
+        sim.add_particles(0, [[10.0, 10.0]] * 3, [3.0] * 3, [1.5] * 3)  # capacity
+
+
+@gpu
+def test_divergence_is_reported():
+    sim = lbm.LBM(lbm.make_config(lbm.LBM_D2Q9, (32, 32, 1)))
+    f = np.zeros((9, 32, 32), np.float32)
+    f[1] = 5.0  # |u| = 5 on every node
+    sim.set_populations(f)
+    sim.step(1)
+    with pytest.raises(lbm.LBMError) as ei:
+        sim.sync()
+    assert ei.value.status == -4
