@@ -1,0 +1,366 @@
+"""Throughput of the penalized-LBM hot path on GB300 (one JSON line on rank 0).
+
+A step is one full time step of the method (fused stream-collide-penalize
+kernel + FP64 particle kernels) over the whole workload.  The default
+workload is the many-particle sedimentation case: D2Q9, 1024 x 4096 box with
+walls, 500 disks R ~ U(6,12), density ratio ~ U(1.1,2.0), tau = 1,
+alpha = 1/tau, gravity 2e-6 (synthetic, seeded).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage fp32|fp16] [--workload many_disks|ensemble|spheres3d]
+
+Under torchrun (N > 1) every rank runs an independent replica (seed = rank):
+the method has no exchange between independent instances, so there is no
+collective on the data path ("scaling": "weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
+FLUID_SRC = os.path.join(ROOT, "paper_2511_01629_gb300", "csrc", "lbm_fluid.cu")
+METRIC = "MLUPS & % HBM peak: FP32 vs FP16-store (err≤1e-3); adjoint/forward time ratio"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workloads(name, seed):
+    from paper_2511_01629_gb300 import workloads as W
+    if name == "many_disks":
+        return [W.many_disks(seed)]
+    if name == "ensemble":
+        return W.ensemble(seed)
+    if name == "spheres3d":
+        return [W.spheres3d(seed)]
+    if name == "single_disk":
+        return [W.single_disk(seed)]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(name, ws, storage):
+    nodes = sum(w.nodes for w in ws)
+    parts = sum(w.num_particles for w in ws)
+    if name == "many_disks":
+        text = "D2Q9 many-particle sedimentation 1024x4096, 500 disks R~U(6,12), ratio~U(1.1,2.0)"
+    elif name == "ensemble":
+        text = f"{len(ws)} D2Q9 sedimentation instances, nx~U{{200..800}}, ny=4nx, 1-50 disks each"
+    elif name == "spheres3d":
+        text = "D3Q19 256x256x512 box, 8 spheres R=10, ratio 1.5"
+    else:
+        text = name
+    return {"workload": text, "lattice": "D2Q9" if ws[0].D == 2 else "D3Q19", "nodes": nodes,
+            "particles": parts, "instances": len(ws), "tau": ws[0].tau, "alpha": ws[0].alpha,
+            "storage": storage, "steps_per_graph": 16}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        smax = max((float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def bytes_per_node(D, storage):
+    q = 8 if D == 2 else 18  # stored populations (the rest population is never read back)
+    return 2 * q * (2 if storage == "fp16" else 4)
+
+
+def measured_peak():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_launch(storage, workload):
+    """DRAM bytes per fluid-kernel launch from the committed ncu capture, or None
+    when the kernel source changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256(open(FLUID_SRC, "rb").read()).hexdigest()[:16]
+        key = f"{workload}/{storage}"
+        if rec.get("fluid_src_sha") != h or key not in rec.get("bytes_per_launch", {}):
+            return None
+        return float(rec["bytes_per_launch"][key])
+    except Exception:
+        return None
+
+
+def cpu_oracle_mlups(ws, steps):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from harness import oracle_config
+    w = ws[0]
+    sim = oracle.Sim(oracle_config(w))
+    if w.num_particles:
+        sim.add_particles(w.pos, w.radius, w.ratio)
+    sim.step(1)  # warm-up (page-in, first owner map)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return w.nodes * steps / dt / 1e6, dt
+
+
+def run_reference(args, ws_n, rank):
+    if rank != 0:
+        return
+    ws = make_workloads(args.workload, 0)
+    w = ws[0]
+    budget = 90.0  # seconds of oracle work for the whole run
+    per_step = w.nodes / 4e6
+    k = max(1, min(args.steps, int(budget / per_step) - args.warmup))
+    w_steps = min(args.warmup, 2)
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from harness import oracle_config
+    sim = oracle.Sim(oracle_config(w))
+    if w.num_particles:
+        sim.add_particles(w.pos, w.radius, w.ratio)
+    if w_steps:
+        sim.step(w_steps)
+    t0 = time.perf_counter()
+    sim.step(k)
+    dt = time.perf_counter() - t0
+    mlups = w.nodes * k / dt / 1e6
+    sample = f"{k} full oracle steps of instance 0 after {w_steps} warm-up steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws_n,
+        "steps": k, "warmup": w_steps, "ms_per_step": dt / k * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": describe(args.workload, ws, "fp64"),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--workload", default="many_disks",
+                    choices=["many_disks", "ensemble", "spheres3d", "single_disk"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fp16-leg", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="fluid kernel shape vec,rows,warps (vec 0 = TMA pipeline) instead of autotuning")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only launch the fluid kernel (for profiler launch lists)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2511_01629_gb300 import lbm
+    lbm.build() if not os.path.exists(lbm.LIB_PATH) else None
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def leg(storage, steps, warmup, with_e2e, with_kernel):
+        ws = make_workloads(args.workload, rank)
+        st = lbm.LBM_FP16 if storage == "fp16" else lbm.LBM_FP32
+        sim = lbm.from_workloads(ws, st)
+        if args.shape:
+            sim.set_kernel_shape(*[int(v) for v in args.shape.split(",")])
+        elif not args.no_autotune:
+            sim.autotune(3)
+        sim.set_graphs(16)
+        stream = sim.stream
+        nodes = sim.total_nodes
+        out = {"nodes": nodes, "shape": sim.kernel_shape(), "launches_per_step": sim.launches_per_step()}
+        if args.kernel_only:
+            for _ in range(warmup + steps):
+                sim.fluid_step_only()
+            torch.cuda.synchronize()
+            return out, sim
+        sim.step(warmup)
+        sim.sync()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        out.update(ms=ms, clocks=clk.summary())
+        if with_kernel:
+            # the dominant kernel alone, same stream, averaged over launches
+            for _ in range(3):
+                sim.fluid_step_only()
+            torch.cuda.synchronize()
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(steps):
+                sim.fluid_step_only()
+            k1.record(stream)
+            torch.cuda.synchronize()
+            out["kernel_ms"] = k0.elapsed_time(k1) / steps
+        if with_e2e:
+            blob = sim.save_state()
+            pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+            pinned.numpy()[:] = memoryview(blob)
+            import ctypes
+            npart = sum(sim.num_particles(i) for i in range(len(ws)))
+            ke = max(10, steps // 4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = lbm.lib().lbm_load_state(sim._h, ctypes.c_void_p(pinned.data_ptr()), len(blob))
+            sim._check(rc)
+            for _ in range(ke):
+                sim.step(1)
+                for i in range(len(ws)):
+                    sim.particles(i)  # d2h of the step's result (synchronises)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out["e2e"] = {"value": nodes * ke / dt / 1e6, "unit": "MLUPS",
+                          "h2d_bytes_per_step": len(blob) / ke,
+                          "d2h_bytes_per_step": npart * (5 * 3 * 8 + 4),
+                          "steps": ke, "note": "state uploaded once from pinned host memory inside "
+                          "the timed region, particle state read back after every step"}
+        return out, sim
+
+    storage = args.storage
+    res, sim = leg(storage, args.steps, args.warmup, not args.no_e2e, True)
+    if args.kernel_only:
+        sim.close()
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "shape": res["shape"]}))
+        return
+    ws0 = make_workloads(args.workload, 0)
+    D = ws0[0].D
+    nodes = res["nodes"]
+    ms_step = res["ms"] / args.steps
+    value = world * nodes * args.steps / (res["ms"] / 1e3) / 1e6
+    peak, peak_kind = measured_peak()
+    bpn = bytes_per_node(D, storage)
+    kms = res["kernel_ms"]
+    achieved = nodes * bpn / (kms / 1e3) / 1e9
+    traffic = traffic_per_launch(storage, args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if storage == "fp32" else "f32 (fp16 storage)",
+        "data": "synthetic",
+        "config": dict(describe(args.workload, ws0, storage),
+                       l2="no flush: the ping-pong population state (%.0f MB) exceeds the 129 MB L2"
+                       % (nodes * bpn / 1e6)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_fluid (fused stream-collide-penalize)",
+                     "algorithmic_bytes_per_node": bpn, "kernel_ms": kms,
+                     "peak_kind": f"hbm_gbs of {peak_kind}"},
+        "gpu_launches": res["launches_per_step"] * args.steps,
+        "clocks": res["clocks"],
+        "kernel_shape": {"vec": res["shape"][0], "tile_rows": res["shape"][1], "warps": res["shape"][2]},
+    }
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+        line["e2e"]["value"] *= world
+    sim.close()
+    if storage == "fp32" and not args.no_fp16_leg and args.workload in ("many_disks", "spheres3d"):
+        r16, s16 = leg("fp16", args.steps, args.warmup, False, True)
+        s16.close()
+        v16 = world * r16["nodes"] * args.steps / (r16["ms"] / 1e3) / 1e6
+        b16 = bytes_per_node(D, "fp16")
+        a16 = r16["nodes"] * b16 / (r16["kernel_ms"] / 1e3) / 1e9
+        line["fp16_storage"] = {"value": v16, "unit": "MLUPS", "ms_per_step": r16["ms"] / args.steps,
+                                "roofline": {"achieved": a16, "peak": peak, "frac": a16 / peak,
+                                             "algorithmic_bytes_per_node": b16,
+                                             "kernel_ms": r16["kernel_ms"],
+                                             "traffic": traffic_per_launch("fp16", args.workload)},
+                                "speedup_vs_fp32": v16 / value}
+    line["adjoint_forward_ratio"] = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ws_c = make_workloads(args.workload, 0)
+        steps_c = 3 if ws_c[0].nodes > 1e6 else 20
+        mc, dtc = cpu_oracle_mlups(ws_c, steps_c)
+        line["cpu_baseline"] = {"value": mc, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"{steps_c} FP64 oracle steps of instance 0 "
+                                          f"({ws_c[0].nodes} nodes), {dtc:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -88,7 +88,7 @@ typedef struct {
     double eps_p, eps_w;     /* stiffnesses epsilon_p, epsilon_w; defaults 2 and 1 */
     int K;                   /* predictor-corrector sub-steps (Algorithm 1); default 1 */
     int max_particles;       /* capacity reserved at creation; default 64 */
-    double max_radius;       /* largest particle radius to be added; default 16 */
+    double max_radius;       /* largest particle radius to be added, <= 120; default 16 */
     int fp16_scale_log2;     /* FP16 storage keeps f * 2^k (exact scaling); default 14 */
 } lbm_config;
 
@@ -170,7 +170,10 @@ int lbm_set_graphs(lbm_ctx* ctx, int steps_per_graph); /* 0 = plain launches */
 /* Time each fluid-kernel shape on the current state and keep the fastest.
  * The state is not changed.  reps: timed launches per shape. */
 int lbm_autotune(lbm_ctx* ctx, int reps);
-/* Current fluid-kernel shape: nodes per thread, tile rows, warps per block. */
+/* Fluid-kernel shape.  vec = 0 is the TMA-staged pipeline (one producer warp
+ * filling a ring of shared-memory stages by tensor copies, `warps` consumer
+ * warps, tile rows 4 or 8); vec = 1/2/4 (FP32) or 2/4/8 (FP16) is the
+ * register path with vec nodes per thread and `warps` warps per block. */
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);
 int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
 /* Kernel launches issued by one lbm_step(ctx, 1) (fluid + particle kernels). */

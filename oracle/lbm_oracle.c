@@ -176,17 +176,36 @@ static int node_inside(const orc_sim* s, int p, const int* xyz) {
     return d2 <= s->R[p] * s->R[p];
 }
 
+/* Particles are visited in index order and a node keeps the first particle
+   that contains it, so the lowest index wins.  Only the nodes of each
+   particle's bounding box [X - R - 1, X + R + 1] (wrapped on periodic axes)
+   are tested; every node outside it is farther than R from the centre. */
 static void build_owner(orc_sim* s) {
-    int nz = s->c.D == 3 ? s->c.n[2] : 1;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < s->c.n[1]; ++j)
-            for (int i = 0; i < s->c.n[0]; ++i) {
-                int xyz[3] = {i, j, k};
-                int own = -1;
-                for (int p = 0; p < s->np && own < 0; ++p)
-                    if (node_inside(s, p, xyz)) own = p;
-                s->owner[nidx(s, i, j, k)] = own;
+    int D = s->c.D;
+    for (long x = 0; x < s->N; ++x) s->owner[x] = -1;
+    for (int p = 0; p < s->np; ++p) {
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+            if (d >= D) continue;
+            lo[d] = (int)floor(s->X[3 * p + d] - s->R[p]) - 1;
+            hi[d] = (int)floor(s->X[3 * p + d] + s->R[p]) + 1;
+            if (!s->c.periodic[d]) {
+                if (lo[d] < 0) lo[d] = 0;
+                if (hi[d] > s->c.n[d] - 1) hi[d] = s->c.n[d] - 1;
+            } else if (hi[d] - lo[d] + 1 > s->c.n[d]) {
+                lo[d] = 0;
+                hi[d] = s->c.n[d] - 1;
             }
+        }
+        for (int k = lo[2]; k <= hi[2]; ++k)
+            for (int j = lo[1]; j <= hi[1]; ++j)
+                for (int i = lo[0]; i <= hi[0]; ++i) {
+                    int xyz[3] = {i, j, k};
+                    for (int d = 0; d < 3; ++d) xyz[d] = ((xyz[d] % s->c.n[d]) + s->c.n[d]) % s->c.n[d];
+                    long x = nidx(s, xyz[0], xyz[1], xyz[2]);
+                    if (s->owner[x] < 0 && node_inside(s, p, xyz)) s->owner[x] = p;
+                }
+    }
 }
 
 void orc_owner_map(orc_sim* s, int* owner) {

@@ -9,6 +9,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/lbmpen.h"
 #include "lbm_internal.cuh"
 
@@ -29,6 +32,12 @@ cudaError_t launch_substep(const InstDesc* insts, const PartRef* refs, int ntota
                            int K, int last, int lpar, const Shape& sh, cudaStream_t st);
 cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int lpar,
                            const Shape& sh, cudaStream_t st);
+int tma_tile_width(int Q);
+bool tma_rows_ok(int rows);
+int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages);
+cudaError_t launch_fluid_tma(int Q, int fp16, const InstDesc* insts, const void* tmaps,
+                             const uint16_t* tile_inst, int ntiles, int par, const Shape& sh,
+                             int commit, int grid, int* tile_ctr, int stages, cudaStream_t st);
 }  // namespace lbmpen
 
 using namespace lbmpen;
@@ -49,7 +58,7 @@ struct Instance {
     int ntile[3] = {1, 1, 1};
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
-    DevBuf f[2], prec, lcnt[2], lent[2], partial, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk,
+    DevBuf f[2], prec, lcnt[2], lent[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk,
         Ubar, Xf;
     std::vector<double> hR;  // radii (validation)
 };
@@ -62,14 +71,15 @@ struct lbm_ctx {
     lbm_allocator alloc{};
     bool has_alloc = false;
     std::vector<Instance> inst;
-    DevBuf d_insts, d_tile_inst, d_tile_ctr, d_status, d_refs;
+    DevBuf d_insts, d_tile_inst, d_tile_ctr, d_status, d_refs, d_tmaps;
     int ntiles = 0, np_total = 0;
     int par = 0;
     long long steps = 0;
-    Shape shape{4, 4, 1, 4, 0};
+    Shape shape{4, 4, 1, 4, 0, 0, 3, 128};
     int grid = 0, num_sms = 0;
     int graph_steps = 16;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;  // capture stream (capture is not allowed on the legacy stream)
     bool graph_ok[2] = {false, false};
     bool failed = false;
     std::string err;
@@ -147,7 +157,10 @@ int validate(const lbm_config* c, char* why, size_t nwhy) {
         return bad("delta, eps_p and eps_w must be positive");
     if (c->K < 1 || c->K > 64) return bad("K must lie in 1 .. 64");
     if (c->max_particles < 0 || c->max_particles > (1 << 20)) return bad("max_particles out of range");
-    if (!(c->max_radius >= 2.0)) return bad("max_radius must be >= 2");
+    if ((double)c->n[0] * c->n[1] * c->n[2] * 19 > 2.0e9)
+        return bad("at most 2e9 stored populations per instance");
+    if (!(c->max_radius >= 2.0) || c->max_radius > MAX_RADIUS)
+        return bad("max_radius must lie in [2, 120]");
     if (c->fp16_scale_log2 < 0 || c->fp16_scale_log2 > 24) return bad("fp16_scale_log2 in 0 .. 24");
     for (int d = 0; d < 3; ++d) {
         if (c->bc[d] != LBM_PERIODIC && c->bc[d] != LBM_WALL) return bad("bc must be PERIODIC or WALL");
@@ -166,11 +179,11 @@ int validate(const lbm_config* c, char* why, size_t nwhy) {
 }
 
 int max_slots(const Instance& I, int D, const Shape& sh) {
-    const int T[3] = {32 * sh.vec, sh.ty, sh.tz};
+    const int T[3] = {sh.tw, sh.ty, sh.tz};
     int k = 1;
     for (int d = 0; d < D; ++d) {
         const int span = (int)ceil(2 * I.cfg.max_radius) + 4;
-        k *= std::min(span / T[d] + 2, I.ntile[d]);
+        k *= std::min(span / T[d] + 3, I.ntile[d]);  // a wrapped interval splits in two
     }
     return std::min(std::max(k, 1), MAXK);
 }
@@ -221,7 +234,8 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.list_cnt[1] = P<int>(I.lcnt[1]);
     d.list_ent[0] = P<uint32_t>(I.lent[0]);
     d.list_ent[1] = P<uint32_t>(I.lent[1]);
-    d.partial = P<double>(I.partial);
+    d.partial = P<long long>(I.partial);
+    d.partial_scratch = P<long long>(I.partial_scratch);
     d.X = P<double>(I.X);
     d.U = P<double>(I.U);
     d.W = P<double>(I.W);
@@ -260,10 +274,13 @@ int upload_descs(lbm_ctx* ctx) {
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->d_insts.ptr, h.data(), sizeof(InstDesc) * h.size(),
                        cudaMemcpyHostToDevice, ctx->st));
-    // particle reference table for the per-particle kernels
+    // particle reference table for the per-particle kernels, padded per
+    // instance to whole blocks of 8 so that no block straddles two instances
     std::vector<PartRef> refs;
-    for (int i = 0; i < (int)ctx->inst.size(); ++i)
+    for (int i = 0; i < (int)ctx->inst.size(); ++i) {
         for (int p = 0; p < ctx->inst[i].np; ++p) refs.push_back({i, p});
+        while (refs.size() % 8) refs.push_back({-1, 0});
+    }
     ctx->np_total = (int)refs.size();
     rc = dalloc(ctx, ctx->d_refs, sizeof(PartRef) * std::max<size_t>(refs.size(), 1));
     if (rc) return rc;
@@ -286,11 +303,75 @@ int republish(lbm_ctx* ctx) {
     return LBM_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// One tensor map per instance and population buffer: the stored populations
+// as a [Q-1][nz][ny][pitch] tensor (x innermost, dim = nx so that boxes read
+// zeros beyond the last node), boxes of (tile width + 2 halo) x ty (x tz).
+int build_tmaps(lbm_ctx* ctx) {
+    auto enc = tmap_encoder();
+    if (!enc) return set_err(ctx, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available%s");
+    const size_t ss = ctx->fp16 ? 2 : 4;
+    const int halo = 16 / (int)ss;
+    std::vector<CUtensorMap> maps(2 * ctx->inst.size());
+    for (size_t i = 0; i < ctx->inst.size(); ++i) {
+        Instance& I = ctx->inst[i];
+        for (int b = 0; b < 2; ++b) {
+            cuuint64_t dims[4], strides[3];
+            cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+            cuuint32_t rank;
+            dims[0] = (cuuint64_t)I.n[0];
+            dims[1] = (cuuint64_t)I.n[1];
+            strides[0] = (cuuint64_t)I.pitch * ss;
+            box[0] = (cuuint32_t)(ctx->shape.tw + 2 * halo);
+            box[1] = (cuuint32_t)ctx->shape.ty;
+            if (ctx->D == 2) {
+                rank = 3;
+                dims[2] = (cuuint64_t)(ctx->Q - 1);
+                strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
+                box[2] = 1;
+            } else {
+                rank = 4;
+                dims[2] = (cuuint64_t)I.n[2];
+                dims[3] = (cuuint64_t)(ctx->Q - 1);
+                strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
+                strides[2] = (cuuint64_t)I.pitch * I.n[1] * I.n[2] * ss;
+                box[2] = (cuuint32_t)ctx->shape.tz;
+                box[3] = 1;
+            }
+            CUresult r = enc(&maps[2 * i + b],
+                             ctx->fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                             rank, I.f[b].ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return set_err(ctx, LBM_ERR_CUDA, "tensor map encoding failed%s");
+        }
+    }
+    int rc = dalloc(ctx, ctx->d_tmaps, sizeof(CUtensorMap) * maps.size());
+    if (rc) return rc;
+    CK(cudaMemcpy(ctx->d_tmaps.ptr, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                  cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 // Tile grid, tile -> instance table, tile lists and partial slots for a shape.
-int configure_shape(lbm_ctx* ctx, const Shape& sh) {
+int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
+    Shape sh = sh_in;
+    if (ctx->D == 2) sh.tz = 1;
+    sh.tw = sh.tma ? tma_tile_width(ctx->Q) : 32 * sh.vec;
     ctx->shape = sh;
-    if (ctx->D == 2) ctx->shape.tz = 1;
-    const int T[3] = {32 * sh.vec, sh.ty, ctx->D == 2 ? 1 : sh.tz};
+    const int T[3] = {sh.tw, sh.ty, sh.tz};
     int tile0 = 0;
     std::vector<uint16_t> tab;
     for (int i = 0; i < (int)ctx->inst.size(); ++i) {
@@ -310,8 +391,11 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh) {
             if ((rc = dalloc(ctx, I.lent[b], sizeof(uint32_t) * (size_t)I.ntiles * LIST_CAP))) return rc;
             CK(cudaMemsetAsync(I.lcnt[b].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
         }
-        if ((rc = dalloc(ctx, I.partial, sizeof(double) * (size_t)std::max(I.cap, 1) * I.maxk * NPV)))
-            return rc;
+        const size_t pb = sizeof(long long) * (size_t)std::max(I.cap, 1) * I.maxk * NPV;
+        const size_t had = I.partial.bytes;
+        if ((rc = dalloc(ctx, I.partial, pb))) return rc;
+        if ((rc = dalloc(ctx, I.partial_scratch, pb))) return rc;
+        if (I.partial.bytes != had) CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
     }
     ctx->ntiles = tile0;
     int rc = dalloc(ctx, ctx->d_tile_inst, sizeof(uint16_t) * tab.size());
@@ -319,38 +403,49 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh) {
     CK(cudaMemcpyAsync(ctx->d_tile_inst.ptr, tab.data(), sizeof(uint16_t) * tab.size(),
                        cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    const int occ = fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, ctx->shape);
-    ctx->grid = std::max(1, occ) * ctx->num_sms;
+    const int occ = sh.tma ? fluid_tma_blocks_per_sm(ctx->Q, ctx->fp16, sh, sh.stages)
+                           : fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, sh);
+    if (occ < 1) return set_err(ctx, LBM_ERR_INVALID, "kernel shape does not fit on an SM%s");
+    ctx->grid = occ * ctx->num_sms;
+    if (sh.tma && (rc = build_tmaps(ctx))) return rc;
     if ((rc = upload_descs(ctx))) return rc;
     invalidate_graphs(ctx);
     return republish(ctx);
 }
 
 Shape default_shape(int Q, int fp16) {
-    if (Q == 9) return fp16 ? Shape{8, 4, 1, 4, 0} : Shape{4, 4, 1, 4, 0};
-    return fp16 ? Shape{4, 2, 2, 4, 0} : Shape{2, 2, 2, 4, 0};
+    // TMA-staged pipeline: 8 consumer warps, 3 stages
+    if (Q == 9) return Shape{fp16 ? 8 : 4, 8, 1, 8, 1, 1, 3, 128};
+    return Shape{fp16 ? 4 : 2, 2, 2, 4, 1, 1, 3, 64};
 }
 
-int enqueue_fluid(lbm_ctx* ctx, int commit) {
+int enqueue_fluid(lbm_ctx* ctx, int commit, cudaStream_t st) {
     const Shape& sh = ctx->shape;
+    if (sh.tma) {
+        CK(launch_fluid_tma(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), ctx->d_tmaps.ptr,
+                            P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, ctx->par, sh, commit,
+                            ctx->grid, P<int>(ctx->d_tile_ctr), sh.stages, st));
+        return LBM_OK;
+    }
     CK(launch_fluid(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), P<uint16_t>(ctx->d_tile_inst),
                     ctx->ntiles, ctx->par, sh, commit, sh.persistent, ctx->grid,
-                    P<int>(ctx->d_tile_ctr), ctx->st));
+                    P<int>(ctx->d_tile_ctr), st));
     return LBM_OK;
 }
+int enqueue_fluid(lbm_ctx* ctx, int commit) { return enqueue_fluid(ctx, commit, ctx->st); }
 
-// One full time step on the stream (no synchronisation).
-int enqueue_step(lbm_ctx* ctx) {
-    int rc = enqueue_fluid(ctx, 1);
+// One full time step on stream st (no synchronisation).
+int enqueue_step(lbm_ctx* ctx, cudaStream_t st) {
+    int rc = enqueue_fluid(ctx, 1, st);
     if (rc) return rc;
     if (ctx->np_total > 0) {
         const InstDesc* di = P<InstDesc>(ctx->d_insts);
         const PartRef* dr = P<PartRef>(ctx->d_refs);
-        CK(launch_finalize(di, dr, ctx->np_total, ctx->D, ctx->st));
+        CK(launch_finalize(di, dr, ctx->np_total, ctx->D, st));
         const int K = ctx->inst[0].cfg.K;
         for (int k = 0; k < K; ++k)
             CK(launch_substep(di, dr, ctx->np_total, ctx->D, k & 1, K, k == K - 1, ctx->par ^ 1,
-                              ctx->shape, ctx->st));
+                              ctx->shape, st));
     }
     ctx->par ^= 1;
     ctx->steps += 1;
@@ -379,6 +474,7 @@ int read_status(lbm_ctx* ctx) {
     if (st & ST_DIVERGED) return set_err(ctx, LBM_ERR_DIVERGED, "the flow diverged (|u| >= 0.5 or non-finite)%s");
     if (st & ST_PARTICLE) return set_err(ctx, LBM_ERR_PARTICLE, "a particle centre crossed a wall%s");
     if (st & ST_DISPLACEMENT) return set_err(ctx, LBM_ERR_DIVERGED, "a particle moved faster than 0.5 per step%s");
+    if (st & ST_TIMEOUT) return set_err(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up%s");
     return set_err(ctx, LBM_ERR_CAPACITY, "a tile overlaps more particles than its list holds%s");
 }
 
@@ -386,7 +482,7 @@ void destroy_all(lbm_ctx* ctx) {
     invalidate_graphs(ctx);
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
-                          &I.partial, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
+                          &I.partial, &I.partial_scratch, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
                           &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
@@ -395,6 +491,7 @@ void destroy_all(lbm_ctx* ctx) {
     dfree(ctx, ctx->d_tile_ctr);
     dfree(ctx, ctx->d_status);
     dfree(ctx, ctx->d_refs);
+    dfree(ctx, ctx->d_tmaps);
 }
 
 int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
@@ -409,7 +506,9 @@ int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
     if ((rc = dalloc(ctx, I.prec, sizeof(PRec) * c))) return rc;
     if ((rc = dalloc(ctx, I.Xk, sizeof(double) * 6 * c))) return rc;
     if ((rc = dalloc(ctx, I.Xf, sizeof(float) * 8 * c))) return rc;
-    if ((rc = dalloc(ctx, I.partial, sizeof(double) * c * std::max(I.maxk, 1) * NPV))) return rc;
+    if ((rc = dalloc(ctx, I.partial, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
+    if ((rc = dalloc(ctx, I.partial_scratch, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
+    CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
     return LBM_OK;
 }
 
@@ -484,7 +583,6 @@ int lbm_create_batch(const lbm_config* cfgs, int n, const lbm_allocator* alloc, 
     }
     ctx->inst.resize(n);
     ctx->shape = default_shape(ctx->Q, ctx->fp16);
-    if (n > 1) ctx->shape.persistent = 1;
     const size_t ssz = ctx->fp16 ? 2 : 4;
     int rc = LBM_OK;
     for (int i = 0; i < n && rc == LBM_OK; ++i) {
@@ -604,10 +702,11 @@ int lbm_step(lbm_ctx* ctx, int nsteps) {
             if (!ctx->graph_ok[p]) {
                 cudaGraph_t g = nullptr;
                 const long long s0 = ctx->steps;
-                CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+                if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+                CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
                 int err = LBM_OK;
-                for (int k = 0; k < G && err == LBM_OK; ++k) err = enqueue_step(ctx);
-                cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+                for (int k = 0; k < G && err == LBM_OK; ++k) err = enqueue_step(ctx, ctx->cap);
+                cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
                 ctx->steps = s0;
                 ctx->par = p;
                 if (err) return err;
@@ -621,7 +720,7 @@ int lbm_step(lbm_ctx* ctx, int nsteps) {
             ctx->steps += G;  // G is even: the parity returns to p
             nsteps -= G;
         } else {
-            if ((rc = enqueue_step(ctx))) return rc;
+            if ((rc = enqueue_step(ctx, ctx->st))) return rc;
             nsteps -= 1;
         }
     }
@@ -853,7 +952,7 @@ int lbm_set_graphs(lbm_ctx* ctx, int steps_per_graph) {
 
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps) {
     if (!ctx) return LBM_ERR_INVALID;
-    if (vec) *vec = ctx->shape.vec;
+    if (vec) *vec = ctx->shape.tma ? 0 : ctx->shape.vec;
     if (tile_rows) *tile_rows = ctx->shape.ty * ctx->shape.tz;
     if (warps) *warps = ctx->shape.warps;
     return LBM_OK;
@@ -866,11 +965,14 @@ static bool shape_ok(const lbm_ctx* ctx, int vec) {
 int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps) {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    if (!shape_ok(ctx, vec) || tile_rows < 1 || tile_rows > 64 || warps < 1 || warps > 8)
+    if ((vec != 0 && !shape_ok(ctx, vec)) || tile_rows < 1 || tile_rows > 64 || warps < 1 || warps > 8)
         return set_err(ctx, LBM_ERR_INVALID, "unsupported kernel shape%s");
     Shape s = ctx->shape;
-    s.vec = vec;
+    s.tma = vec == 0;
+    if (vec) s.vec = vec;
     s.warps = warps;
+    if (s.tma && !tma_rows_ok(tile_rows))
+        return set_err(ctx, LBM_ERR_INVALID, "TMA tiles hold 4 or 8 rows%s");
     if (ctx->D == 2) {
         s.ty = tile_rows;
         s.tz = 1;
@@ -896,21 +998,36 @@ int lbm_autotune(lbm_ctx* ctx, int reps) {
             for (int warps : {2, 4, 8})
                 for (int pers : {0, 1}) {
                     if (warps > rows) continue;
-                    Shape s{vecs[vi], rows, 1, warps, pers};
+                    Shape s{vecs[vi], rows, 1, warps, pers, 0, 0, 0};
                     if (ctx->D == 3) {
                         s.tz = rows >= 4 ? 2 : 1;
                         s.ty = rows / s.tz;
                     }
                     cand.push_back(s);
                 }
+    for (int rows : {4, 8})
+        for (int warps : {4, 8})
+            for (int stages : {2, 3, 4}) {
+                Shape s{ctx->shape.vec, rows, 1, warps, 1, 1, stages, 0};
+                if (ctx->D == 3) {
+                    s.tz = rows >= 4 ? 2 : 1;
+                    s.ty = rows / s.tz;
+                }
+                cand.push_back(s);
+            }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     Shape bests = ctx->shape;
     for (const Shape& s : cand) {
-        if ((rc = configure_shape(ctx, s))) break;
-        if (fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, ctx->shape) < 1) continue;
+        if ((rc = configure_shape(ctx, s))) {
+            if (rc == LBM_ERR_INVALID) {  // does not fit: skip this shape
+                rc = LBM_OK;
+                continue;
+            }
+            break;
+        }
         for (int w = 0; w < 2; ++w)
             if ((rc = enqueue_fluid(ctx, 0))) break;
         if (rc) break;
@@ -955,6 +1072,7 @@ void lbm_destroy(lbm_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->st);
     destroy_all(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
 }
 

@@ -1,0 +1,471 @@
+// Device helpers shared by the fused fluid kernels (register path and TMA
+// path) and the export kernels of lbmpen.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbmpen {
+
+// ------------------------------------------------------------ vector I/O ---
+template <class S, int V> struct VecIO;
+
+template <int V> struct VecIO<float, V> {
+    static __device__ __forceinline__ void load(const float* p, float (&o)[V], float) {
+        if constexpr (V == 1) {
+            o[0] = __ldg(p);
+        } else if constexpr (V == 2) {
+            float2 t = __ldg(reinterpret_cast<const float2*>(p));
+            o[0] = t.x; o[1] = t.y;
+        } else {
+            static_assert(V == 4, "fp32 vector width");
+            float4 t = __ldg(reinterpret_cast<const float4*>(p));
+            o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+        }
+    }
+    static __device__ __forceinline__ void store(float* p, const float (&v)[V], float) {
+        if constexpr (V == 1) {
+            p[0] = v[0];
+        } else if constexpr (V == 2) {
+            *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        } else {
+            *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    static __device__ __forceinline__ float load1(const float* p, float) { return __ldg(p); }
+};
+
+template <int V> struct VecIO<__half, V> {
+    static_assert(V == 2 || V == 4 || V == 8, "fp16 vector width");
+    static __device__ __forceinline__ void load(const __half* p, float (&o)[V], float s) {
+        if constexpr (V == 2) {
+            unsigned int t = __ldg(reinterpret_cast<const unsigned int*>(p));
+            float2 a = __half22float2(*reinterpret_cast<__half2*>(&t));
+            o[0] = a.x * s; o[1] = a.y * s;
+        } else if constexpr (V == 4) {
+            uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+            float2 a = __half22float2(*reinterpret_cast<__half2*>(&t.x));
+            float2 b = __half22float2(*reinterpret_cast<__half2*>(&t.y));
+            o[0] = a.x * s; o[1] = a.y * s; o[2] = b.x * s; o[3] = b.y * s;
+        } else {
+            uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+            unsigned int w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float2 a = __half22float2(*reinterpret_cast<__half2*>(&w[i]));
+                o[2 * i] = a.x * s; o[2 * i + 1] = a.y * s;
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(__half* p, const float (&v)[V], float s) {
+        unsigned int w[V / 2];
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            __half2 h = __floats2half2_rn(v[2 * i] * s, v[2 * i + 1] * s);
+            w[i] = *reinterpret_cast<unsigned int*>(&h);
+        }
+        if constexpr (V == 2) {
+            *reinterpret_cast<unsigned int*>(p) = w[0];
+        } else if constexpr (V == 4) {
+            *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        } else {
+            *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    static __device__ __forceinline__ float load1(const __half* p, float s) {
+        return __half2float(p[0]) * s;
+    }
+};
+
+__device__ __forceinline__ float to_float_scaled(float v, float) { return v; }
+__device__ __forceinline__ float to_float_scaled(__half v, float s) { return __half2float(v) * s; }
+
+template <class S> __device__ __forceinline__ S to_store(float v, float s);
+template <> __device__ __forceinline__ float to_store<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half>(float v, float s) {
+    return __float2half_rn(v * s);
+}
+
+// -------------------------------------------------------- indicator test ---
+// Candidate particle of a tile, staged in shared memory.
+struct Cand {
+    int ref[3];
+    float frac[3];
+    float R2lo, R2hi;
+    float a[3];
+    int p;  // particle index within the instance
+    int k;  // partial slot of this tile in the particle's bounding box
+};
+
+// Per-tile geometry and collision constants, copied out of the instance
+// descriptor into registers: the hot loops must not reload them after every
+// population store (the compiler cannot prove the stores do not alias them).
+struct Geo {
+    int n[3];
+    int per[3];
+    const PRec* prec;
+};
+struct CollP {
+    float keep, fpref, alpha;
+};
+__device__ __forceinline__ Geo make_geo(const InstDesc& in) {
+    Geo g;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = in.n[d];
+        g.per[d] = in.periodic[d];
+    }
+    g.prec = in.prec;
+    return g;
+}
+__device__ __forceinline__ CollP make_collp(const InstDesc& in) { return CollP{in.keep, in.fpref, in.alpha}; }
+
+__device__ __forceinline__ int wrap_int(int d, int n, int per) {
+    if (per) {
+        int h = n >> 1;
+        if (d > h) d -= n;
+        else if (d < -h) d += n;
+    }
+    return d;
+}
+
+// Exact FP64 form of Eq. 9 on the lattice, identical operation by operation
+// to the reference definition: d2 = ((0 + dx*dx) + dy*dy) + dz*dz with each
+// dx = x - X_d taken to the minimum image on periodic axes, then d2 <= R*R.
+// Separate roundings (no fused multiply-add) via the _rn intrinsics.
+template <int D>
+__device__ __noinline__ bool inside_exact(const PRec* __restrict__ pr, int x, int y, int z, int nx,
+                                          int ny, int nz, int pmask) {
+    const int xyz[3] = {x, y, z}, n[3] = {nx, ny, nz};
+    double d2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        double dx = __dsub_rn((double)xyz[d], pr->X[d]);
+        if ((pmask >> d) & 1) {
+            double half = 0.5 * (double)n[d];
+            if (dx > half) dx = __dsub_rn(dx, (double)n[d]);
+            else if (dx < -half) dx = __dadd_rn(dx, (double)n[d]);
+        }
+        d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
+    }
+    return d2 <= pr->R2;
+}
+template <int D>
+__device__ __forceinline__ bool inside_exact(const Geo& g, const PRec& pr, const int* xyz) {
+    return inside_exact<D>(&pr, xyz[0], xyz[1], xyz[2], g.n[0], g.n[1], g.n[2],
+                           g.per[0] | (g.per[1] << 1) | (g.per[2] << 2));
+}
+
+// Owner of a node among the tile's candidates: lowest particle index whose
+// solid domain holds the node, or -1.  Float filter with a safety band; nodes
+// in the band take the exact FP64 test.
+template <int D>
+__device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int ncand,
+                                        const int* xyz, int* slot) {
+    int best = -1, bslot = -1;
+    for (int c = 0; c < ncand; ++c) {
+        const Cand& cd = cand[c];
+        if (best >= 0 && cd.p > best) continue;
+        float d2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            int di = wrap_int(xyz[d] - cd.ref[d], in.n[d], in.per[d]);
+            float dx = (float)di - cd.frac[d];
+            d2 = fmaf(dx, dx, d2);
+        }
+        bool inside;
+        if (d2 < cd.R2lo) inside = true;
+        else if (d2 > cd.R2hi) inside = false;
+        else inside = inside_exact<D>(in, in.prec[cd.p], xyz);
+        if (inside && (best < 0 || cd.p < best)) {
+            best = cd.p;
+            bslot = c;
+        }
+    }
+    *slot = bslot;
+    return best;
+}
+
+// ------------------------------------------------------------- collision ---
+// BGK with Guo forcing (Eqs. 10, 13, 14) and, on solid nodes, the penalty
+// source of Eq. 17, with A_q = w_q / cs^2:
+//   feq_q = A_q (p - u.u/2 + c.u + 1.5 (c.u)^2)                      (Eq. 13)
+//   F_q   = (1 - 1/2tau) A_q ((c.a)(1 + 3 c.u) - u.a)                 (Eq. 14)
+//   S_q   = 1.5 alpha A_q (Pi_neq : c c - tr(Pi_neq) / 3)             (Eq. 17)
+//   f*_q  = (1 - 1/tau) f_q + feq_q / tau + F_q + chi S_q             (Eq. 10)
+// and p recovered from the stored populations (Eq. 15b) as
+//   p = (sum_{q>=1} f_q - (1.5 - 0.5 sum A) u.u) / sum A,
+// the inverse of feq for these coefficients.  Opposite velocities share c.u,
+// c.a and p - u.u/2 + 1.5 (c.u)^2, so the work goes pair by pair.
+struct CollK {
+    float keep;       // 1 - 1/tau
+    float omk;        // 1/tau
+    float A[2];       // A for the two weight classes (axis, diagonal/edge)
+    float fA[2];      // (1 - 1/2tau) A
+    float alpha;
+};
+template <int Q>
+__device__ __forceinline__ CollK make_collk(const CollP& in) {
+    using L = Lat<Q>;
+    CollK k;
+    k.keep = in.keep;
+    k.omk = 1.0f - in.keep;
+    const float A[2] = {L::A(1), L::A(Q == 9 ? 5 : 7)};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        // A stays exact (sum A c_x^2 = 1): 1/tau multiplies separately, so no
+        // rounded product of the two can bias the momentum of feq
+        k.A[i] = A[i];
+        k.fA[i] = in.fpref * A[i];
+    }
+    k.alpha = in.alpha;
+    return k;
+}
+
+// c_q . v for a compile-time velocity q, without adding zeros
+template <int Q, int q>
+__device__ __forceinline__ float cdot(const float* v) {
+    using L = Lat<Q>;
+    constexpr int c0 = L::c(q, 0), c1 = L::c(q, 1), c2 = L::c(q, 2);
+    float r;
+    if constexpr (c0 != 0) {
+        r = c0 > 0 ? v[0] : -v[0];
+        if constexpr (c1 != 0) r = c1 > 0 ? r + v[1] : r - v[1];
+        if constexpr (c2 != 0) r = c2 > 0 ? r + v[2] : r - v[2];
+    } else if constexpr (c1 != 0) {
+        r = c1 > 0 ? v[1] : -v[1];
+        if constexpr (c2 != 0) r = c2 > 0 ? r + v[2] : r - v[2];
+    } else {
+        r = c2 > 0 ? v[2] : -v[2];
+    }
+    return r;
+}
+
+// first velocity of each opposite pair: q odd in both numberings except D2Q9,
+// where pairs are (1,3), (2,4), (5,7), (6,8)
+template <int Q> __host__ __device__ constexpr bool pair_head(int q) {
+    return Q == 9 ? (q == 1 || q == 2 || q == 5 || q == 6) : (q & 1) == 1;
+}
+
+template <int Q, int q>
+__device__ __forceinline__ void collide_pair(float* f, const float* u, const float* a, float base,
+                                             float ua, const CollK& k) {
+    if constexpr (q < Q) {
+        if constexpr (pair_head<Q>(q)) {
+            using L = Lat<Q>;
+            constexpr int qo = L::opp(q);
+            constexpr int cls = (Q == 9 ? q >= 5 : q >= 7) ? 1 : 0;
+            const float cu = cdot<Q, q>(u), ca = cdot<Q, q>(a);
+            const float t = fmaf(1.5f * cu, cu, base);
+            const float eq = t + cu, eo = t - cu;                     // feq / A
+            const float Fq = fmaf(ca, fmaf(3.0f, cu, 1.0f), -ua);     // F / fA
+            const float Fo = fmaf(-ca, fmaf(-3.0f, cu, 1.0f), -ua);
+            f[q - 1] = fmaf(k.keep, f[q - 1], fmaf(k.omk, k.A[cls] * eq, k.fA[cls] * Fq));
+            f[qo - 1] = fmaf(k.keep, f[qo - 1], fmaf(k.omk, k.A[cls] * eo, k.fA[cls] * Fo));
+        }
+        collide_pair<Q, q + 1>(f, u, a, base, ua, k);
+    }
+}
+
+// Penalty source on a solid node, added to the post-collision f (which no
+// longer holds the pre-collision values: they are passed in fpre).
+template <int Q>
+__device__ __forceinline__ void add_penalty(float* f, const float* fpre, const float* u, float base,
+                                            float alpha) {
+    using L = Lat<Q>;
+    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz of Pi_neq
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        float cu = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (L::c(q, d) != 0) cu += L::c(q, d) > 0 ? u[d] : -u[d];
+        const float fn = fpre[q - 1] - L::A(q) * fmaf(1.5f * cu, cu, base + cu);
+        const int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
+        if (cx) P[0] += fn;
+        if (cy) P[1] += fn;
+        if (cz) P[2] += fn;
+        if (cx * cy) P[3] += cx * cy > 0 ? fn : -fn;
+        if (cx * cz) P[4] += cx * cz > 0 ? fn : -fn;
+        if (cy * cz) P[5] += cy * cz > 0 ? fn : -fn;
+    }
+    const float trP = (P[0] + P[1] + P[2]) * (1.0f / 3.0f);
+    const float sfac = 1.5f * alpha;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
+        float pcc = 0.f;
+        if (cx) pcc += P[0];
+        if (cy) pcc += P[1];
+        if (cz) pcc += P[2];
+        if (cx * cy) pcc += 2.0f * (cx * cy > 0 ? P[3] : -P[3]);
+        if (cx * cz) pcc += 2.0f * (cx * cz > 0 ? P[4] : -P[4]);
+        if (cy * cz) pcc += 2.0f * (cy * cz > 0 ? P[5] : -P[5]);
+        f[q - 1] += sfac * L::A(q) * (pcc - trP);
+    }
+}
+
+// Moments of the stored populations, written out without adding zeros.
+template <int Q>
+__device__ __forceinline__ void moments(const float* f, float& s, float* m) {
+    if constexpr (Q == 9) {
+        const float d13 = f[0] - f[2], d24 = f[1] - f[3], d57 = f[4] - f[6], d68 = f[5] - f[7];
+        s = ((f[0] + f[2]) + (f[1] + f[3])) + ((f[4] + f[6]) + (f[5] + f[7]));
+        m[0] = d13 + (d57 - d68);
+        m[1] = d24 + (d57 + d68);
+        m[2] = 0.f;
+    } else {
+        // D3Q19 pairs (1,2) x, (3,4) y, (5,6) z, (7,8) xy, (9,10) x-y, (11,12) xz,
+        // (13,14) x-z, (15,16) yz, (17,18) y-z; d_k = f_head - f_tail
+        const float dx = f[0] - f[1], dy = f[2] - f[3], dz = f[4] - f[5];
+        const float dxy = f[6] - f[7], dxmy = f[8] - f[9], dxz = f[10] - f[11];
+        const float dxmz = f[12] - f[13], dyz = f[14] - f[15], dymz = f[16] - f[17];
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 18; i += 2) {
+            a0 += f[i];
+            a1 += f[i + 1];
+        }
+        s = a0 + a1;
+        m[0] = dx + ((dxy + dxmy) + (dxz + dxmz));
+        m[1] = dy + ((dxy - dxmy) + (dyz + dymz));
+        m[2] = dz + ((dxz - dxmz) + (dyz - dymz));
+    }
+}
+
+// One node: f holds the stored populations q = 1..Q-1 (index q-1) after
+// streaming; on return it holds f*.  u and p of Eq. 15 are returned.
+template <int Q>
+__device__ __forceinline__ void collide(float* f, const float* a, bool solid, const CollK& k,
+                                        float* u_out, float* p_out) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    constexpr float inv_sa = (float)(1.0 / L::SUMA);
+    constexpr float kuu = (float)(1.5 - 0.5 * L::SUMA);
+    float s, m[3];
+    moments<Q>(f, s, m);
+    float u[3];
+    u[0] = fmaf(0.5f, a[0], m[0]);  // Eq. 15a
+    u[1] = fmaf(0.5f, a[1], m[1]);
+    u[2] = D == 3 ? fmaf(0.5f, a[2], m[2]) : 0.f;
+    const float uu = D == 3 ? fmaf(u[2], u[2], fmaf(u[1], u[1], u[0] * u[0])) : fmaf(u[1], u[1], u[0] * u[0]);
+    const float p = fmaf(-kuu, uu, s) * inv_sa;  // Eq. 15b
+    const float ua = D == 3 ? fmaf(u[2], a[2], fmaf(u[1], a[1], u[0] * a[0])) : fmaf(u[1], a[1], u[0] * a[0]);
+    const float base = fmaf(-0.5f, uu, p);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u_out[d] = u[d];
+    *p_out = p;
+    if (solid) {
+        float fpre[Q - 1];
+#pragma unroll
+        for (int q = 0; q < Q - 1; ++q) fpre[q] = f[q];
+        collide_pair<Q, 1>(f, u, a, base, ua, k);
+        add_penalty<Q>(f, fpre, u, base, k.alpha);
+    } else {
+        collide_pair<Q, 1>(f, u, a, base, ua, k);
+    }
+}
+
+// Exact fixed-point image round(u * 2^FXBITS) of a velocity component, with
+// integer operations only (the value is clamped to |u| < 1/2; a larger or
+// non-finite velocity is reported as divergence by the caller).
+__device__ __forceinline__ long long to_fx(float u) {
+    u = fminf(fmaxf(u, -0.49999997f), 0.49999997f);
+    const int b = __float_as_int(u);
+    const int e = (b >> 23) & 0xff;
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0x7fffff) | 0x800000);
+    const int sh = e - 150 + FXBITS;  // |u| = m * 2^(e - 150)
+    long long v;
+    if (sh >= 0) v = m << sh;
+    else if (sh > -25) v = (m + (1LL << (-sh - 1))) >> (-sh);
+    else v = 0;
+    return b < 0 ? -v : v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums of Eq. 22 of one warp over the nodes (V per lane) owned by each
+// candidate, added with integer atomics straight into the particle's slot for
+// this tile (integer adds do not depend on their order; the finalize kernel
+// reads the slot and clears it for the next step).
+template <int D, int V>
+__device__ __forceinline__ void row_partials(const Geo& in, const Cand* cand, int ncand,
+                                             long long* partial, int maxk, const int* slot,
+                                             const float (*uv)[V], int xl, int y, int z, int lane) {
+    for (int c = 0; c < ncand; ++c) {
+        bool mine = false;
+#pragma unroll
+        for (int e = 0; e < V; ++e) mine |= slot[e] == c;
+        if (!__any_sync(0xffffffffu, mine)) continue;
+        const Cand& cd = cand[c];
+        int icnt = 0, id[3] = {0, 0, 0}, idd[6] = {0, 0, 0, 0, 0, 0};
+        long long su[3] = {0, 0, 0}, sl[3] = {0, 0, 0};
+        const int dy = wrap_int(y - cd.ref[1], in.n[1], in.per[1]);
+        const int dz = D == 3 ? wrap_int(z - cd.ref[2], in.n[2], in.per[2]) : 0;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            if (slot[e] != c) continue;
+            const int dx = wrap_int(xl + e - cd.ref[0], in.n[0], in.per[0]);
+            long long ux[3] = {to_fx(uv[0][e]), to_fx(uv[1][e]), D == 3 ? to_fx(uv[2][e]) : 0};
+            icnt += 1;
+            id[0] += dx; id[1] += dy; id[2] += dz;
+            idd[0] += dx * dx; idd[1] += dy * dy; idd[2] += dz * dz;
+            idd[3] += dx * dy; idd[4] += dx * dz; idd[5] += dy * dz;
+            su[0] += ux[0]; su[1] += ux[1]; su[2] += ux[2];
+            sl[2] += (long long)dx * ux[1] - (long long)dy * ux[0];
+            if (D == 3) {
+                sl[0] += (long long)dy * ux[2] - (long long)dz * ux[1];
+                sl[1] += (long long)dz * ux[0] - (long long)dx * ux[2];
+            }
+        }
+        long long v[NPV];
+        v[0] = __reduce_add_sync(0xffffffffu, icnt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[1 + k] = (k < D) ? __reduce_add_sync(0xffffffffu, id[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const bool need = D == 3 || k == 0 || k == 1 || k == 3;
+            v[4 + k] = need ? __reduce_add_sync(0xffffffffu, idd[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            v[10 + k] = (k < D) ? warp_sum_ll(su[k]) : 0;
+            v[13 + k] = (D == 3 || k == 2) ? warp_sum_ll(sl[k]) : 0;
+        }
+        if (lane == 0) {
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(
+                partial + ((long long)cd.p * maxk + cd.k) * NPV);
+#pragma unroll
+            for (int k = 0; k < NPV; ++k)
+                if (v[k] != 0) atomicAdd(dst + k, (unsigned long long)v[k]);
+        }
+    }
+}
+
+template <int Q, class S>
+__device__ __noinline__ float pull_scalar(const InstDesc& in, const S* fin, int q, int x, int y, int z) {
+    using L = Lat<Q>;
+    const int c[3] = {L::c(q, 0), L::c(q, 1), L::c(q, 2)};
+    int src[3] = {x - c[0], y - c[1], z - c[2]};
+    int axis = -1, face = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (src[d] < 0 || src[d] >= in.n[d]) {
+            if (in.periodic[d]) src[d] = src[d] < 0 ? src[d] + in.n[d] : src[d] - in.n[d];
+            else if (axis < 0) { axis = d; face = src[d] < 0 ? 0 : 1; }
+        }
+    }
+    if (axis >= 0) {
+        const int qo = L::opp(q);
+        const long long off = ((long long)z * in.n[1] + y) * in.pitch + x;
+        return VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (long long)(qo - 1) * in.qstride + off,
+                                                       in.s_load) + in.wterm[axis][face][q];
+    }
+    const long long off = ((long long)src[2] * in.n[1] + src[1]) * in.pitch + src[0];
+    return VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (long long)(q - 1) * in.qstride + off, in.s_load);
+}
+
+}  // namespace lbmpen

@@ -10,8 +10,9 @@
 //   tile lists   list_cnt[2][ntiles], list_ent[2][ntiles][cap]: for each
 //                tile the particles whose bounding box overlaps it, built by
 //                the particle kernel for the next step (no per-node mask);
-//   partials     partial[np][maxk][NPV] FP64: per particle and per tile of its
-//                bounding box, the sums of Eq. 22 over that tile.
+//   partials     partial[np][maxk][NPV] int64: per particle and per tile of its
+//                bounding box, the sums of Eq. 22 over that tile, exact in
+//                fixed point (velocities in units of 2^-FXBITS).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -48,31 +49,54 @@ __host__ __device__ constexpr float d3q19_w(int q) {
     return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
 
+// FP32 coefficients A_q = w_q / cs^2 = 3 w_q.  1/3 and 1/12 are not binary
+// fractions, so the nearest floats would give sum_q A_q c_qx^2 = 1 + 7e-9 and
+// every collision would scale the momentum of feq by that factor (a drift
+// of 1e-5 over 1000 steps).  The pairs below are the closest floats with
+// sum_q A_q c_qx^2 = 1 exactly (2 A1 + 4 A2 = 1 in D2Q9, 2 Aa + 8 Ae = 1 in
+// D3Q19), so Eqs. 12 and 14 keep u exactly up to the rounding of each operation.
+constexpr float D2Q9_A1 = 0x1.555556p-2f;  // axis, ~1/3
+constexpr float D2Q9_A2 = 0x1.555554p-4f;  // diagonal, ~1/12
+constexpr float D3Q19_AA = 0x1.555554p-3f; // axis, ~1/6
+constexpr float D3Q19_AE = 0x1.555556p-4f; // edge, ~1/12
+
 template <int Q> struct Lat;
 template <> struct Lat<9> {
     static constexpr int D = 2;
     __host__ __device__ static constexpr int c(int q, int d) { return d2q9_c(q, d); }
     __host__ __device__ static constexpr int opp(int q) { return d2q9_opp(q); }
     __host__ __device__ static constexpr float w(int q) { return d2q9_w(q); }
+    __host__ __device__ static constexpr float A(int q) { return q <= 4 ? D2Q9_A1 : D2Q9_A2; }
+    // sum over the stored velocities q >= 1 of A_q
+    static constexpr double SUMA = 4.0 * (double)D2Q9_A1 + 4.0 * (double)D2Q9_A2;
 };
 template <> struct Lat<19> {
     static constexpr int D = 3;
     __host__ __device__ static constexpr int c(int q, int d) { return d3q19_c(q, d); }
     __host__ __device__ static constexpr int opp(int q) { return d3q19_opp(q); }
     __host__ __device__ static constexpr float w(int q) { return d3q19_w(q); }
+    __host__ __device__ static constexpr float A(int q) { return q <= 6 ? D3Q19_AA : D3Q19_AE; }
+    static constexpr double SUMA = 6.0 * (double)D3Q19_AA + 12.0 * (double)D3Q19_AE;
 };
 
 // ------------------------------------------------------------- descriptors --
-// Number of FP64 values per (particle, tile) partial:
+// Values per (particle, tile) partial, all int64:
 //   0 count, 1-3 sum d, 4-9 sum d_i d_j (xx, yy, zz, xy, xz, yz),
-//   10-12 sum u, 13-15 sum d x u;  d = node - floor(X) (integer offsets).
+//   10-12 sum u, 13-15 sum d x u;  d = node - floor(X) (integer offsets),
+//   u in fixed point round(u * 2^FXBITS).  Integer sums are exact and do not
+//   depend on the order of addition, so the reductions are deterministic;
+//   they are converted to FP64 once per particle.  With |u| < 1/2 (larger
+//   velocities stop the run as diverged) and radii <= MAX_RADIUS the largest
+//   particle total stays below 2^62.
 constexpr int NPV = 16;
+constexpr int FXBITS = 40;
+constexpr double MAX_RADIUS = 120.0;
 constexpr int LIST_CAP = 64;   // particles listed per tile (overflow -> LBM_ERR_CAPACITY)
 constexpr int KBITS = 10;      // list entry = particle << KBITS | slot
 constexpr int MAXK = 1 << KBITS;
 
 // Status word bits (device), mapped to lbm_status on the host.
-enum { ST_DIVERGED = 1, ST_CAPACITY = 2, ST_PARTICLE = 4, ST_DISPLACEMENT = 8 };
+enum { ST_DIVERGED = 1, ST_CAPACITY = 2, ST_PARTICLE = 4, ST_DISPLACEMENT = 8, ST_TIMEOUT = 16 };
 
 // Particle record read by the fluid kernel; written by the particle kernel
 // for the next step.
@@ -108,7 +132,8 @@ struct InstDesc {
     PRec* prec;               // [np]
     int* list_cnt[2];         // [ntiles]
     uint32_t* list_ent[2];    // [ntiles][LIST_CAP]
-    double* partial;          // [np][maxk][NPV]
+    long long* partial;       // [np][maxk][NPV], cleared by the finalize kernel
+    long long* partial_scratch;  // same shape: sink of launches that do not advance the state
     // particle state (FP64), [np][3] unless noted
     double* X;
     double* U;                // U^{n-1} entering the step, U^n after it
@@ -133,10 +158,13 @@ struct InstDesc {
 // Kernel shape of the fused fluid kernel: a tile is (32 * vec) x rows_y x rows_z
 // nodes; each warp handles whole x-rows of the tile.
 struct Shape {
-    int vec;     // nodes per thread along x (vector width)
+    int vec;     // register path: nodes per thread along x (vector width)
     int ty, tz;  // tile rows along y and z
-    int warps;   // warps per block
-    int persistent;  // 1: grid-stride blocks pulling tiles from a work counter
+    int warps;   // warps per block (consumer warps on the TMA path)
+    int persistent;  // register path: blocks pulling tiles from a work counter
+    int tma;     // 1: TMA-staged pipeline kernel
+    int stages;  // TMA path: shared-memory ring stages
+    int tw;      // tile width in nodes (32 * vec, or the TMA box width without halo)
 };
 
 // Particle index -> (instance, local index) for the per-particle kernels.
@@ -145,6 +173,6 @@ struct PartRef {
     int p;
 };
 
-__host__ __device__ inline int tile_w(const Shape& s) { return 32 * s.vec; }
+__host__ __device__ inline int tile_w(const Shape& s) { return s.tw; }
 
 }  // namespace lbmpen
