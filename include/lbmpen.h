@@ -185,6 +185,37 @@ int lbm_fluid_step_only(lbm_ctx* ctx);
 long long lbm_steps_done(const lbm_ctx* ctx);
 long long lbm_total_nodes(const lbm_ctx* ctx);
 
+/* Rigid-body projection without allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory where
+ * they need the projection (a host application that owns all device memory,
+ * a frame loop that must not stall on the device synchronisation implied by
+ * cudaMalloc/cudaFree).  It computes the U and omega of Eq. 22 of a given
+ * velocity field over given particles, with the owner rule of the context
+ * path (lowest index wins), and allocates nothing: its scratch is a fixed
+ * array of LBM_NOALLOC_MAX_PARTICLES * 16 int64 sums compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.
+ *   dim 2 or 3; n (host, 3 ints) nodes per axis; periodic (host, 3 ints);
+ *   u   device, dim * N floats [d][z][y][x] (the layout of lbm_get_fields);
+ *   np  particles, 0 .. LBM_NOALLOC_MAX_PARTICLES (more: LBM_ERR_INVALID);
+ *   pos device, np * dim doubles; radius device, np doubles, each in
+ *       [0, max_radius] with max_radius <= 120 (and 2 max_radius + 4 <= n on
+ *       periodic axes);
+ *   vel device out, np * dim doubles; omega device out, np (2D) or np * 3
+ *       doubles; count device out, np ints (nodes owned by each particle);
+ *   stream cudaStream_t the work is issued on.
+ * The call returns after the results are written (it waits for the stream).
+ * Its first call on a device looks up the device address of the scratch
+ * array for that device; make that first call outside any stream capture.
+ * Every call uses the same array, so calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results.  Returns
+ * LBM_ERR_INVALID for a radius above max_radius and LBM_ERR_CAPACITY when a
+ * particle overlaps more than 64 particles of lower index. */
+#define LBM_NOALLOC_MAX_PARTICLES 4096
+int lbm_rigid_projection_noalloc(int dim, const int* n, const int* periodic, const float* u, int np,
+                                 const double* pos, const double* radius, double max_radius,
+                                 double* vel, double* omega, int* count, void* stream);
+
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(int status);
 void lbm_destroy(lbm_ctx* ctx);

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "liblbmpen.so")
-_SOURCES = ["lbm_fluid.cu", "lbm_fluid_tma.cu", "lbm_particles.cu", "lbm_api.cu"]
+_SOURCES = ["lbm_fluid.cu", "lbm_fluid_tma.cu", "lbm_particles.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC"]
 
