@@ -27,7 +27,10 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
-FLUID_SRC = os.path.join(ROOT, "paper_2511_01629_gb300", "csrc", "lbm_fluid.cu")
+CSRC = os.path.join(ROOT, "paper_2511_01629_gb300", "csrc")
+# sources the fused fluid kernel is built from (the traffic record is void once they change)
+FLUID_SRCS = [os.path.join(CSRC, f) for f in ("lbm_fluid_tma.cu", "lbm_fluid.cu", "lbm_common.cuh",
+                                               "lbm_internal.cuh")]
 METRIC = "MLUPS & % HBM peak: FP32 vs FP16-store (err≤1e-3); adjoint/forward time ratio"
 
 
@@ -126,13 +129,20 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def fluid_src_sha():
+    hh = hashlib.sha256()
+    for f in FLUID_SRCS:
+        hh.update(open(f, "rb").read())
+    return hh.hexdigest()[:16]
+
+
 def traffic_per_launch(storage, workload):
     """DRAM bytes per fluid-kernel launch from the committed ncu capture, or None
     when the kernel source changed since the capture."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
-        h = hashlib.sha256(open(FLUID_SRC, "rb").read()).hexdigest()[:16]
+        h = fluid_src_sha()
         key = f"{workload}/{storage}"
         if rec.get("fluid_src_sha") != h or key not in rec.get("bytes_per_launch", {}):
             return None
@@ -325,7 +335,7 @@ def main():
                        % (nodes * bpn / 1e6)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_fluid (fused stream-collide-penalize)",
+                     "kernel": "k_fluid_tma (fused stream-collide-penalize)",
                      "algorithmic_bytes_per_node": bpn, "kernel_ms": kms,
                      "peak_kind": f"hbm_gbs of {peak_kind}"},
         "gpu_launches": res["launches_per_step"] * args.steps,

@@ -26,10 +26,9 @@ cudaError_t launch_pack(int Q, int fp16, const InstDesc* insts, int inst, long l
                         const float* src, cudaStream_t st);
 cudaError_t launch_unpack(int Q, int fp16, const InstDesc* insts, int inst, long long N, int par,
                           float* dst, cudaStream_t st);
-cudaError_t launch_finalize(const InstDesc* insts, const PartRef* refs, int ntotal, int D,
-                            cudaStream_t st);
-cudaError_t launch_substep(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int src,
-                           int K, int last, int lpar, const Shape& sh, cudaStream_t st);
+int particle_blocks_resident(int num_sms);
+cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int K,
+                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st);
 cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int lpar,
                            const Shape& sh, cudaStream_t st);
 int tma_tile_width(int Q);
@@ -58,9 +57,10 @@ struct Instance {
     int ntile[3] = {1, 1, 1};
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
-    DevBuf f[2], prec, lcnt[2], lent[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk,
+    DevBuf f[2], prec, lcnt[2], lent[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
         Ubar, Xf;
-    std::vector<double> hR;  // radii (validation)
+    std::vector<double> hR;      // radii (validation)
+    std::vector<double> hratio;  // density ratios (per-particle constants)
 };
 
 }  // namespace
@@ -71,7 +71,7 @@ struct lbm_ctx {
     lbm_allocator alloc{};
     bool has_alloc = false;
     std::vector<Instance> inst;
-    DevBuf d_insts, d_tile_inst, d_tile_ctr, d_status, d_refs, d_tmaps;
+    DevBuf d_insts, d_tile_inst, d_tile_ctr, d_status, d_refs, d_tmaps, d_gridbar;
     int ntiles = 0, np_total = 0;
     int par = 0;
     long long steps = 0;
@@ -249,12 +249,16 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.Xk = P<double>(I.Xk);
     d.Ubar = P<double>(I.Ubar);
     d.Xf = P<float>(I.Xf);
+    d.pconst = P<double>(I.pconst);
+    d.Xsf = P<float>(I.Xsf);
+    d.invc = P<double>(I.invc);
     d.rho_f = c.rho_f;
     d.gmag = sqrt(c.g_grav[0] * c.g_grav[0] + c.g_grav[1] * c.g_grav[1] + c.g_grav[2] * c.g_grav[2]);
     d.delta = c.delta;
     d.eps_p = c.eps_p;
     d.eps_w = c.eps_w;
     d.K = c.K;
+    d.hK = 1.0 / c.K;
     d.status = P<int>(ctx->d_status);
     return d;
 }
@@ -291,11 +295,34 @@ int upload_descs(lbm_ctx* ctx) {
     return LBM_OK;
 }
 
+// Per-particle constants of the update: 1 - rho_f/rho_s (buoyancy-reduced
+// gravity), C/eps_p and C/eps_w with C = (rho_s - rho_f)|g| (Eqs. 19-20),
+// 1/delta, 1/rho_s (the mass is rho_s times the node count) and R.
+int upload_pconst(lbm_ctx* ctx, Instance& I) {
+    if (I.np == 0) return LBM_OK;
+    const lbm_config& c = I.cfg;
+    const double g = sqrt(c.g_grav[0] * c.g_grav[0] + c.g_grav[1] * c.g_grav[1] + c.g_grav[2] * c.g_grav[2]);
+    std::vector<double> pc(PCONST_N * (size_t)I.np, 0.0);
+    for (int p = 0; p < I.np; ++p) {
+        const double C = (I.hratio[p] - 1.0) * c.rho_f * g;
+        double* q = pc.data() + PCONST_N * p;
+        q[PC_GFAC] = 1.0 - 1.0 / I.hratio[p];
+        q[PC_CPAIR] = C / c.eps_p;
+        q[PC_CWALL] = C / c.eps_w;
+        q[PC_INVDELTA] = 1.0 / c.delta;
+        q[PC_INVRHOS] = 1.0 / (I.hratio[p] * c.rho_f);
+        q[PC_R] = I.hR[p];
+    }
+    CK(cudaMemcpy(I.pconst.ptr, pc.data(), sizeof(double) * pc.size(), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 // Re-publish every particle into the tile lists of the current parity.
 int republish(lbm_ctx* ctx) {
     for (auto& I : ctx->inst) {
         if (I.np == 0) continue;
         CK(cudaMemsetAsync(I.lcnt[ctx->par].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
+        CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
     }
     if (ctx->np_total > 0)
         CK(launch_publish(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
@@ -439,13 +466,10 @@ int enqueue_step(lbm_ctx* ctx, cudaStream_t st) {
     int rc = enqueue_fluid(ctx, 1, st);
     if (rc) return rc;
     if (ctx->np_total > 0) {
-        const InstDesc* di = P<InstDesc>(ctx->d_insts);
-        const PartRef* dr = P<PartRef>(ctx->d_refs);
-        CK(launch_finalize(di, dr, ctx->np_total, ctx->D, st));
         const int K = ctx->inst[0].cfg.K;
-        for (int k = 0; k < K; ++k)
-            CK(launch_substep(di, dr, ctx->np_total, ctx->D, k & 1, K, k == K - 1, ctx->par ^ 1,
-                              ctx->shape, st));
+        const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
+        CK(launch_particles(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
+                            K, ctx->par ^ 1, ctx->shape, P<GridBar>(ctx->d_gridbar), fused, st));
     }
     ctx->par ^= 1;
     ctx->steps += 1;
@@ -483,7 +507,7 @@ void destroy_all(lbm_ctx* ctx) {
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
                           &I.partial, &I.partial_scratch, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
-                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf};
+                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
     dfree(ctx, ctx->d_insts);
@@ -492,6 +516,7 @@ void destroy_all(lbm_ctx* ctx) {
     dfree(ctx, ctx->d_status);
     dfree(ctx, ctx->d_refs);
     dfree(ctx, ctx->d_tmaps);
+    dfree(ctx, ctx->d_gridbar);
 }
 
 int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
@@ -506,6 +531,9 @@ int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
     if ((rc = dalloc(ctx, I.prec, sizeof(PRec) * c))) return rc;
     if ((rc = dalloc(ctx, I.Xk, sizeof(double) * 6 * c))) return rc;
     if ((rc = dalloc(ctx, I.Xf, sizeof(float) * 8 * c))) return rc;
+    if ((rc = dalloc(ctx, I.pconst, sizeof(double) * PCONST_N * c))) return rc;
+    if ((rc = dalloc(ctx, I.invc, sizeof(double) * c))) return rc;
+    if ((rc = dalloc(ctx, I.Xsf, sizeof(float) * 8 * c))) return rc;
     if ((rc = dalloc(ctx, I.partial, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
     if ((rc = dalloc(ctx, I.partial_scratch, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
     CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
@@ -603,6 +631,8 @@ int lbm_create_batch(const lbm_config* cfgs, int n, const lbm_allocator* alloc, 
     }
     if (rc == LBM_OK) rc = dalloc(ctx, ctx->d_tile_ctr, sizeof(int) * 2);
     if (rc == LBM_OK) rc = dalloc(ctx, ctx->d_status, sizeof(int) * 4);
+    if (rc == LBM_OK) rc = dalloc(ctx, ctx->d_gridbar, sizeof(GridBar));
+    if (rc == LBM_OK) cudaMemsetAsync(ctx->d_gridbar.ptr, 0, sizeof(GridBar), ctx->st);
     if (rc == LBM_OK) {
         cudaMemsetAsync(ctx->d_tile_ctr.ptr, 0, sizeof(int) * 2, ctx->st);
         cudaMemsetAsync(ctx->d_status.ptr, 0, sizeof(int) * 4, ctx->st);
@@ -686,6 +716,8 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
     CK(cudaStreamSynchronize(ctx->st));
     I.np += n;
     I.hR.insert(I.hR.end(), radius, radius + n);
+    I.hratio.insert(I.hratio.end(), ratio, ratio + n);
+    if ((rc = upload_pconst(ctx, I))) return rc;
     if ((rc = upload_descs(ctx))) return rc;
     invalidate_graphs(ctx);
     return republish(ctx);
@@ -930,7 +962,9 @@ int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
         CK(cudaMemcpy(I.R.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
         r += sizeof(double) * I.np;
         CK(cudaMemcpy(I.ratio.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
+        I.hratio.assign(reinterpret_cast<const double*>(r), reinterpret_cast<const double*>(r) + I.np);
         r += sizeof(double) * I.np;
+        if ((rc = upload_pconst(ctx, I))) return rc;
         CK(cudaMemcpy(I.count.ptr, r, sizeof(int) * I.np, cudaMemcpyHostToDevice));
         r += sizeof(int) * I.np;
     }
@@ -1054,7 +1088,9 @@ int lbm_autotune(lbm_ctx* ctx, int reps) {
 
 int lbm_launches_per_step(const lbm_ctx* ctx) {
     if (!ctx) return 0;
-    return 1 + (ctx->np_total > 0 ? 1 + ctx->inst[0].cfg.K : 0);
+    if (ctx->np_total == 0) return 1;
+    const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
+    return 1 + (fused ? 1 : 1 + ctx->inst[0].cfg.K);
 }
 
 long long lbm_steps_done(const lbm_ctx* ctx) { return ctx ? ctx->steps : 0; }

@@ -185,6 +185,63 @@ __device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int nca
     return best;
 }
 
+// Candidates whose solid domain can reach the 32-node row segment starting
+// at x0 of row (y, z): a uniform test per candidate instead of a test per
+// node.  Bit c set = candidate c may own a node of the segment (ncand <= 32).
+template <int D>
+__device__ __forceinline__ unsigned segment_candidates(const Geo& g, const Cand* cand, int ncand, int x0,
+                                                       int y, int z) {
+    unsigned act = 0;
+    for (int c = 0; c < ncand; ++c) {
+        const Cand& cd = cand[c];
+        const float dy = (float)wrap_int(y - cd.ref[1], g.n[1], g.per[1]) - cd.frac[1];
+        float rest = cd.R2hi - dy * dy;
+        if (D == 3) {
+            const float dz = (float)wrap_int(z - cd.ref[2], g.n[2], g.per[2]) - cd.frac[2];
+            rest -= dz * dz;
+        }
+        if (rest < 0.f) continue;
+        const float hw = sqrtf(rest) + 1.0f;
+        // nearest distance along x from the centre to the segment [x0, x0 + 31]
+        const float dx0 = (float)wrap_int(x0 - cd.ref[0], g.n[0], g.per[0]) - cd.frac[0];
+        if (dx0 > hw || dx0 + 31.0f < -hw) {
+            if (!g.per[0]) continue;
+        }
+        act |= 1u << c;
+    }
+    return act;
+}
+
+// Owner among the segment's live candidates (bit mask from segment_candidates).
+template <int D>
+__device__ __forceinline__ int owner_masked(const Geo& in, const Cand* cand, unsigned act,
+                                            const int* xyz, int* slot) {
+    int best = -1, bslot = -1;
+    while (act) {
+        const int c = __ffs(act) - 1;
+        act &= act - 1;
+        const Cand& cd = cand[c];
+        if (best >= 0 && cd.p > best) continue;
+        float d2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            int di = wrap_int(xyz[d] - cd.ref[d], in.n[d], in.per[d]);
+            float dx = (float)di - cd.frac[d];
+            d2 = fmaf(dx, dx, d2);
+        }
+        bool inside;
+        if (d2 < cd.R2lo) inside = true;
+        else if (d2 > cd.R2hi) inside = false;
+        else inside = inside_exact<D>(in, in.prec[cd.p], xyz);
+        if (inside && (best < 0 || cd.p < best)) {
+            best = cd.p;
+            bslot = c;
+        }
+    }
+    *slot = bslot;
+    return best;
+}
+
 // ------------------------------------------------------------- collision ---
 // BGK with Guo forcing (Eqs. 10, 13, 14) and, on solid nodes, the penalty
 // source of Eq. 17, with A_q = w_q / cs^2:
@@ -444,6 +501,114 @@ __device__ __forceinline__ void row_partials(const Geo& in, const Cand* cand, in
                 if (v[k] != 0) atomicAdd(dst + k, (unsigned long long)v[k]);
         }
     }
+}
+
+// ----------------------------------------------- per-particle finalisation --
+constexpr double FX_SCALE = 1.0 / (double)(1LL << FXBITS);
+
+// 1/x in FP64 for x in the normal FP32 range: an FP32 reciprocal refined by
+// two Newton steps (within an ulp of the rounded quotient).  A dependent FP64
+// division costs ~10x a fused multiply-add on this GPU.
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Rigid-body projection of particle p (Eq. 22 with rho_s cancelled): the
+// tile partials are exact integers, summed exactly, then converted to FP64.
+// Moments about the integer reference floor(X) are shifted to the centre:
+//   sum r x u = sum d x u - phi x sum u,
+//   sum r r^T = sum d d^T - phi sum d^T - sum d phi^T + n phi phi^T.
+template <int D>
+__device__ void finalize_particle(const InstDesc& in, int p, const long long* v) {
+    const PRec& pr = in.prec[p];
+    // every operand is loaded before the first store, so the loads overlap
+    double X[3] = {0, 0, 0}, Uold[3] = {0, 0, 0}, phi[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        X[d] = pr.X[d];
+        phi[d] = X[d] - (double)pr.ref[d];
+        Uold[d] = in.U[3 * p + d];
+    }
+    const float Rf = (float)in.pconst[PCONST_N * p + PC_R];
+    const double h = in.hK;
+    if (v[0] == 0) {  // no solid node: cannot happen inside the box for R >= 2
+        atomicOr(in.status, ST_PARTICLE);
+        for (int d = 0; d < 3; ++d) {
+            in.Un[3 * p + d] = in.U[3 * p + d];
+            in.Wn[3 * p + d] = 0.0;
+        }
+        in.count[p] = 0;
+        return;
+    }
+    const double cnt = (double)v[0];
+    const double inv = rcp64(cnt);
+    double Su[3] = {0, 0, 0}, Uo[3] = {0, 0, 0}, Wo[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        Su[d] = (double)v[10 + d] * FX_SCALE;
+        Uo[d] = Su[d] * inv;
+    }
+    if (D == 2) {
+        // w_z = sum (r x u)_z / sum |r|^2
+        const double Lz = (double)v[15] * FX_SCALE - (phi[0] * Su[1] - phi[1] * Su[0]);
+        const double Izz = (double)(v[4] + v[5]) - 2.0 * (phi[0] * (double)v[1] + phi[1] * (double)v[2]) +
+                           cnt * (phi[0] * phi[0] + phi[1] * phi[1]);
+        Wo[2] = Lz * rcp64(Izz);
+    } else {
+        const double Sd[3] = {(double)v[1], (double)v[2], (double)v[3]};
+        double Sl[3];
+        for (int d = 0; d < 3; ++d) Sl[d] = (double)v[13 + d] * FX_SCALE;
+        const double Lv[3] = {Sl[0] - (phi[1] * Su[2] - phi[2] * Su[1]),
+                              Sl[1] - (phi[2] * Su[0] - phi[0] * Su[2]),
+                              Sl[2] - (phi[0] * Su[1] - phi[1] * Su[0])};
+        const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+        double rr[3][3];
+        for (int k = 0; k < 6; ++k) {
+            const int i = ii[k], j = jj[k];
+            const double val = (double)v[4 + k] - phi[i] * Sd[j] - phi[j] * Sd[i] + cnt * phi[i] * phi[j];
+            rr[i][j] = val;
+            rr[j][i] = val;
+        }
+        const double tr = rr[0][0] + rr[1][1] + rr[2][2];
+        double I[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) I[i][j] = (i == j ? tr : 0.0) - rr[i][j];
+        const double det = I[0][0] * (I[1][1] * I[2][2] - I[1][2] * I[2][1]) -
+                           I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
+                           I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
+        const double idet = rcp64(det);
+        for (int col = 0; col < 3; ++col) {
+            double M[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) M[r][q] = (q == col) ? Lv[r] : I[r][q];
+            const double dc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                              M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                              M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            Wo[col] = dc * idet;
+        }
+    }
+    bool fast = false;
+    float Xs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        in.Un[3 * p + d] = Uo[d];
+        in.Wn[3 * p + d] = Wo[d];
+        double ub = 0.0;
+        if (d < D) {
+            ub = 0.5 * (Uo[d] + Uold[d]);
+            fast |= !(fabs(ub) < 0.5);
+            Xs[d] = (float)(X[d] + h * ub);
+        }
+        in.Ubar[3 * p + d] = ub;
+        in.Xk[3 * p + d] = X[d];  // sub-step buffer 0 = X^n
+    }
+    reinterpret_cast<float4*>(in.Xf)[p] = make_float4((float)X[0], (float)X[1], (float)X[2], Rf);
+    reinterpret_cast<float4*>(in.Xsf)[p] = make_float4(Xs[0], Xs[1], Xs[2], Rf);
+    in.count[p] = (int)v[0];
+    in.invc[p] = inv;
+    if (fast) atomicOr(in.status, ST_DISPLACEMENT);
 }
 
 template <int Q, class S>

@@ -332,7 +332,14 @@ __global__ void __launch_bounds__(288, (Q == 9 ? 3 : 2)) k_fluid_tma(const InstD
                 }
                 const int xyz[3] = {x, y, z};
                 int own = -1, sl = -1;
-                if (ncand > 0) own = owner_of<D>(geo, cand, ncand, xyz, &sl);
+                unsigned act = 0;
+                if (ncand > 32) {  // more candidates than mask bits: test them all
+                    act = 0xffffffffu;
+                    own = owner_of<D>(geo, cand, ncand, xyz, &sl);
+                } else if (ncand > 0) {
+                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 32, y, z);
+                    if (act) own = owner_masked<D>(geo, cand, act, xyz, &sl);
+                }
                 float a[3] = {h.gdrive[0], h.gdrive[1], h.gdrive[2]};
                 if (own >= 0) {
 #pragma unroll
@@ -354,7 +361,7 @@ __global__ void __launch_bounds__(288, (Q == 9 ? 3 : 2)) k_fluid_tma(const InstD
                         o += qs;
                     }
                 }
-                if (ncand > 0) {
+                if (act) {
                     const int slot[1] = {valid ? sl : -1};
                     const float uv[3][1] = {{u[0]}, {u[1]}, {D == 3 ? u[2] : 0.f}};
                     row_partials<D, 1>(geo, cand, ncand, h.partial, h.maxk, slot, uv, x, y, z, lane);

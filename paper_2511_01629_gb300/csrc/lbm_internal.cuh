@@ -98,6 +98,15 @@ constexpr int MAXK = 1 << KBITS;
 // Status word bits (device), mapped to lbm_status on the host.
 enum { ST_DIVERGED = 1, ST_CAPACITY = 2, ST_PARTICLE = 4, ST_DISPLACEMENT = 8, ST_TIMEOUT = 16 };
 
+// Per-particle constants (host-computed, FP64), stride PCONST_N.
+enum { PC_GFAC = 0, PC_CPAIR = 1, PC_CWALL = 2, PC_INVDELTA = 3, PC_INVRHOS = 4, PC_R = 5, PCONST_N = 8 };
+
+// Grid-wide barrier of the particle kernel (all its blocks are resident).
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
 // Particle record read by the fluid kernel; written by the particle kernel
 // for the next step.
 struct __align__(16) PRec {
@@ -147,10 +156,15 @@ struct InstDesc {
     int* count;               // [np]
     double* Xk;               // [2][np][3] Algorithm-1 sub-step positions
     double* Ubar;             // [np][3]
-    float* Xf;                // [np][4] float copy of X^{k} for the pair filter
+    float* Xf;                // [2][np][4] float copy of X^{k} (w = R) for the pair filter
+    float* Xsf;               // [2][np][4] float copy of X^{k} + Ubar/K (w = R): predicted positions
+    double* pconst;           // [np][8]: 1 - rho_f/rho_s, C/eps_p, C/eps_w, 1/delta,
+                              //   1/(rho_s rho_f... see PCONST_*), R
+    double* invc;             // [np] 1 / (solid nodes at step n)
     double rho_f;
     double gmag;              // |g_grav|
     double delta, eps_p, eps_w;
+    double hK;                // 1 / K
     int K;
     int* status;
 };

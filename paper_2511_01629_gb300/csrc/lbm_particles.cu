@@ -1,150 +1,20 @@
-// Per-particle FP64 kernels of lbmpen: the rigid-body projection (Eq. 22)
-// from the fluid kernel's per-tile partial sums, the predictor-corrector of
-// Algorithm 1 with the repulsive collision forces (Eqs. 19-21), and the
+// Per-particle FP64 kernels of lbmpen: the predictor-corrector of
+// Algorithm 1 with the repulsive collision forces (Eqs. 19-21) and the
 // rebuild of each particle's record and tile-list entries for the next step.
+// (The rigid-body projection of Eq. 22 is finalised at the end of the fused
+// fluid kernel, see lbm_common.cuh.)
 //
-// GB300 runs FP64 at a small fraction of its FP32 rate and the cost of an
-// FP64 instruction is paid per warp, so the serial per-particle arithmetic
-// runs one particle per thread (32 particles per warp instruction).  Only the
-// O(N^2) pair search uses a warp per particle, filtering pairs in FP32 with a
-// margin before the FP64 evaluation of the few pairs within range.
-#include "lbm_internal.cuh"
+// GB300 runs FP64 at a small fraction of its FP32 rate and an FP64
+// instruction costs the same for one lane as for 32, so the serial
+// per-particle arithmetic runs one particle per thread.  The O(N^2) pair
+// search uses a warp per particle and filters pairs in FP32 (positions staged
+// in shared memory) before the FP64 evaluation of the few pairs in range.
+#include "lbm_common.cuh"
 
 namespace lbmpen {
 
-constexpr double FX_SCALE = 1.0 / (double)(1LL << FXBITS);
-
-// Rigid-body projection of particle p (Eq. 22 with rho_s cancelled): the
-// tile partials are exact integers, summed exactly, then converted to FP64.
-// Moments about the integer reference floor(X) are shifted to the centre:
-//   sum r x u = sum d x u - phi x sum u,
-//   sum r r^T = sum d d^T - phi sum d^T - sum d phi^T + n phi phi^T.
-template <int D>
-__device__ void finalize_particle(const InstDesc& in, int p, const long long* v) {
-    const double cnt = (double)v[0];
-    double phi[3], X[3], Uo[3] = {0, 0, 0}, Wo[3] = {0, 0, 0};
-    for (int d = 0; d < 3; ++d) {
-        X[d] = in.X[3 * p + d];
-        phi[d] = d < D ? X[d] - (double)in.prec[p].ref[d] : 0.0;
-    }
-    if (v[0] == 0) {  // no solid node: cannot happen inside the box for R >= 2
-        atomicOr(in.status, ST_PARTICLE);
-        for (int d = 0; d < 3; ++d) {
-            in.Un[3 * p + d] = in.U[3 * p + d];
-            in.Wn[3 * p + d] = 0.0;
-        }
-        in.count[p] = 0;
-        return;
-    }
-    double Sd[3], Su[3], Sl[3];
-    for (int d = 0; d < 3; ++d) {
-        Sd[d] = (double)v[1 + d];
-        Su[d] = (double)v[10 + d] * FX_SCALE;
-        Sl[d] = (double)v[13 + d] * FX_SCALE;
-    }
-    const double inv = 1.0 / cnt;
-    for (int d = 0; d < 3; ++d) Uo[d] = Su[d] * inv;
-    const double Lv[3] = {Sl[0] - (phi[1] * Su[2] - phi[2] * Su[1]),
-                          Sl[1] - (phi[2] * Su[0] - phi[0] * Su[2]),
-                          Sl[2] - (phi[0] * Su[1] - phi[1] * Su[0])};
-    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-    double rr[3][3];
-    for (int k = 0; k < 6; ++k) {
-        const int i = ii[k], j = jj[k];
-        const double val = (double)v[4 + k] - phi[i] * Sd[j] - phi[j] * Sd[i] + cnt * phi[i] * phi[j];
-        rr[i][j] = val;
-        rr[j][i] = val;
-    }
-    if (D == 2) {
-        Wo[2] = Lv[2] / (rr[0][0] + rr[1][1]);
-    } else {
-        const double tr = rr[0][0] + rr[1][1] + rr[2][2];
-        double I[3][3];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) I[i][j] = (i == j ? tr : 0.0) - rr[i][j];
-        const double det = I[0][0] * (I[1][1] * I[2][2] - I[1][2] * I[2][1]) -
-                           I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
-                           I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
-        const double idet = 1.0 / det;
-        for (int col = 0; col < 3; ++col) {
-            double M[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int q = 0; q < 3; ++q) M[r][q] = (q == col) ? Lv[r] : I[r][q];
-            const double dc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
-                              M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                              M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-            Wo[col] = dc * idet;
-        }
-    }
-    bool fast = false;
-    for (int d = 0; d < 3; ++d) {
-        in.Un[3 * p + d] = Uo[d];
-        in.Wn[3 * p + d] = Wo[d];
-        const double ub = 0.5 * (Uo[d] + in.U[3 * p + d]);
-        in.Ubar[3 * p + d] = ub;
-        in.Xk[3 * p + d] = X[d];  // sub-step buffer 0 = X^n
-        fast |= !(fabs(ub) < 0.5);
-    }
-    reinterpret_cast<float4*>(in.Xf)[p] =  // float buffer 0 mirrors Xk buffer 0
-        make_float4((float)X[0], (float)X[1], (float)X[2], (float)in.R[p]);
-    in.count[p] = (int)v[0];
-    if (fast) atomicOr(in.status, ST_DISPLACEMENT);
-}
-
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-constexpr int PB = 8;  // particles per block (one per warp) of the particle kernels
+constexpr int PB = 8;         // particles per block (one per warp)
 constexpr int XCHUNK = 1024;  // particle positions staged in shared memory at a time
-
-// 32 particles per block: the block's warps sum the slot partials of 4
-// particles each (lanes over slots, exact integer tree), then one thread per
-// particle does the FP64 part.
-__global__ void __launch_bounds__(256) k_finalize(const InstDesc* __restrict__ insts,
-                                                  const PartRef* __restrict__ refs, int ntotal,
-                                                  int D) {
-    __shared__ long long tot[PB][NPV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int gp0 = blockIdx.x * PB;
-    for (int t = warp; t < PB; t += nwarps) {
-        const int gp = gp0 + t;
-        if (gp >= ntotal) break;
-        const PartRef r = refs[gp];
-        if (r.inst < 0) continue;  // padding of the instance's last block
-        const InstDesc& in = insts[r.inst];
-        const int nt = min(in.prec[r.p].ntiles, in.maxk);  // overflow is flagged at publish
-        long long v[NPV];
-#pragma unroll
-        for (int k = 0; k < NPV; ++k) v[k] = 0;
-        for (int s = lane; s < nt; s += 32) {
-            longlong2* src = reinterpret_cast<longlong2*>(in.partial + ((long long)r.p * in.maxk + s) * NPV);
-#pragma unroll
-            for (int k = 0; k < NPV / 2; ++k) {
-                const longlong2 a = __ldcg(src + k);
-                v[2 * k] += a.x;
-                v[2 * k + 1] += a.y;
-                src[k] = make_longlong2(0, 0);  // the slot starts the next step at zero
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NPV; ++k) {
-            const long long w = warp_sum_ll(v[k]);
-            if (lane == 0) tot[t][k] = w;
-        }
-    }
-    __syncthreads();
-    if (warp != 0 || lane >= PB) return;
-    const int gp = gp0 + lane;
-    if (gp >= ntotal) return;
-    const PartRef r = refs[gp];
-    if (r.inst < 0) return;
-    const InstDesc& in = insts[r.inst];
-    if (D == 2) finalize_particle<2>(in, r.p, tot[lane]);
-    else finalize_particle<3>(in, r.p, tot[lane]);
-}
 
 // Pair part of Eq. 21 on particle i at two position sets: Xk[src] (F1) and
 // Xk[src] + h Ubar (F2).  The block's particles all belong to one instance;
@@ -153,27 +23,35 @@ __global__ void __launch_bounds__(256) k_finalize(const InstDesc* __restrict__ i
 // a particle by |h Ubar| < 1/2) leaves only pairs near the interaction range
 // for the FP64 evaluation, which follows the reference operation order.
 __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lane, const float4* xs,
-                           int j0, int nj, double* f1, double* f2) {
+                           const float4* xs2, int j0, int nj, double* f1, double* f2) {
     const double* Xb = in.Xk + (long long)src * in.np * 3;
-    const double C = (in.ratio[i] - 1.0) * in.rho_f * in.gmag;
-    if (C == 0.0) return;
+    const double cp = in.pconst[PCONST_N * i + PC_CPAIR];  // C / eps_p of particle i
+    if (cp == 0.0) return;
+    const double inv_delta = in.pconst[PCONST_N * i + PC_INVDELTA];
     const float4 xi = reinterpret_cast<const float4*>(in.Xf)[(long long)src * in.np + i];
-    const float reach = xi.w + (float)in.delta + 2.5f;
+    const float4 xi2 = reinterpret_cast<const float4*>(in.Xsf)[(long long)src * in.np + i];
+    const float reach = xi.w + (float)in.delta + 0.01f;  // FP32 positions carry < 1e-3 error
     const float nf[3] = {(float)in.n[0], (float)in.n[1], (float)in.n[2]};
     const bool per[3] = {in.periodic[0] && in.n[0] > 1, in.periodic[1] && in.n[1] > 1,
                          in.periodic[2] && in.n[2] > 1};
     for (int jj = lane; jj < nj; jj += 32) {
         const int j = j0 + jj;
         if (j == i) continue;
-        const float4 xj = xs[jj];
-        float dv[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
+        bool near[2];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if (per[d]) dv[d] -= nf[d] * rintf(dv[d] / nf[d]);
-        const float lim = reach + xj.w;
-        if (dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] > lim * lim) continue;
+        for (int pass = 0; pass < 2; ++pass) {
+            const float4 a = pass ? xi2 : xi, b = pass ? xs2[jj] : xs[jj];
+            float dv[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (per[d]) dv[d] -= nf[d] * rintf(dv[d] / nf[d]);
+            const float lim = reach + b.w;
+            near[pass] = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] <= lim * lim;
+        }
+        if (!near[0] && !near[1]) continue;
         const double range = in.R[i] + in.R[j] + in.delta;
         for (int pass = 0; pass < 2; ++pass) {
+            if (!near[pass]) continue;
             const double sh = pass ? h : 0.0;
             double dd[3];
             for (int d = 0; d < 3; ++d) {
@@ -189,9 +67,9 @@ __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lan
             const double dij = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
                                               __dmul_rn(dd[2], dd[2])));
             if (dij <= range) {
-                const double sc = (range - dij) / in.delta;
+                const double sc = (range - dij) * inv_delta;
                 double* f = pass ? f2 : f1;
-                for (int d = 0; d < 3; ++d) f[d] += C / in.eps_p * dd[d] * sc * sc;
+                for (int d = 0; d < 3; ++d) f[d] += cp * dd[d] * sc * sc;
             }
         }
     }
@@ -217,10 +95,14 @@ __device__ void gather_pairs(const double* f1, const double* f2, double* F1, dou
 
 // Wall part of Eq. 21 (mirror images across the planes -1/2 and n - 1/2).
 __device__ void wall_force(const InstDesc& in, int i, const double* Xi, double* F) {
-    const double C = (in.ratio[i] - 1.0) * in.rho_f * in.gmag;
-    if (C == 0.0) return;
+    const double cw = in.pconst[PCONST_N * i + PC_CWALL];  // C / eps_w of particle i
+    if (cw == 0.0) return;
+    const double inv_delta = in.pconst[PCONST_N * i + PC_INVDELTA];
+    const float reach = 0.5f * (2.0f * (float)in.R[i] + (float)in.delta) + 0.01f;
     for (int d = 0; d < 3; ++d) {
         if (in.periodic[d] || in.n[d] <= 1) continue;
+        const float xf = (float)Xi[d];  // skip walls farther than (2R + delta)/2
+        if (xf + 0.5f > reach && (float)in.n[d] - 0.5f - xf > reach) continue;
         const double walls[2] = {-0.5, in.n[d] - 0.5};
         for (int face = 0; face < 2; ++face) {
             const double Xim = 2.0 * walls[face] - Xi[d];
@@ -228,8 +110,8 @@ __device__ void wall_force(const InstDesc& in, int i, const double* Xi, double* 
             const double dprime = fabs(diff);
             const double range = 2.0 * in.R[i] + in.delta;
             if (dprime <= range) {
-                const double sc = (range - dprime) / in.delta;
-                F[d] += C / in.eps_w * diff * sc * sc;
+                const double sc = (range - dprime) * inv_delta;
+                F[d] += cw * diff * sc * sc;
             }
         }
     }
@@ -243,8 +125,8 @@ struct AxisTiles {
     int a0, na, b0, nb;
 };
 
-__device__ AxisTiles axis_tiles(double X, double R, int n, int T, int ntile, int periodic) {
-    int lo = (int)floor(X - R) - 1, hi = (int)floor(X + R) + 1;
+__device__ AxisTiles axis_tiles_f(float X, float R, int n, int T, int ntile, int periodic) {
+    int lo = (int)floorf(X - R) - 1, hi = (int)floorf(X + R) + 1;
     AxisTiles t{0, 1, 0, 0};
     if (!periodic) {
         lo = max(lo, 0);
@@ -287,44 +169,44 @@ __device__ __forceinline__ int axis_tile(const AxisTiles& t, int i) {
     return i < t.na ? t.a0 + i : t.b0 + (i - t.na);
 }
 
-// Record and tile-list entries of particle p at its current X and A for the
-// step that reads list parity lpar.  Slots k enumerate the bounding-box tiles
-// x-fastest; no tile is listed twice.  The calling warp's lanes (lane0 ..
-// lane0 + nl - 1) share the list appends; lane0 writes the record.
-__device__ void publish_particle(const InstDesc& in, int p, int lpar, int D, const Shape& sh,
-                                 int lane, int nl) {
-    const double R = in.R[p];
+// Record of particle p at its current X and A for the next fluid step, and
+// the tiles of its bounding box (slots k enumerate them x-fastest; no tile is
+// listed twice).  One thread.
+__device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at) {
+    const double R = in.pconst[PCONST_N * p + PC_R];
+    const float Rf = (float)R;
     const int T[3] = {sh.tw, sh.ty, sh.tz};
-    AxisTiles at[3];
     int cnt[3];
+    PRec pr;
+    const float gfac = (float)in.pconst[PCONST_N * p + PC_GFAC];  // 1 - rho_f / rho_s
     for (int d = 0; d < 3; ++d) {
-        if (d >= D) {
-            at[d] = AxisTiles{0, 1, 0, 0};
-        } else {
-            at[d] = axis_tiles(in.X[3 * p + d], R, in.n[d], T[d], in.ntile[d], in.periodic[d]);
-        }
+        const double X = in.X[3 * p + d];
+        pr.X[d] = X;
+        const int ref = d < D ? __double2int_rd(X) : 0;
+        pr.ref[d] = ref;
+        pr.frac[d] = (float)(X - (double)ref);
+        pr.a[d] = fmaf(gfac, in.ggrav[d], (float)in.A[3 * p + d]);
+        // box [X - R - 1, X + R + 1]: its one-node margin covers the float rounding
+        at[d] = d >= D ? AxisTiles{0, 1, 0, 0}
+                       : axis_tiles_f((float)ref + pr.frac[d], Rf, in.n[d], T[d], in.ntile[d], in.periodic[d]);
         cnt[d] = at[d].na + at[d].nb;
     }
     const int nt = cnt[0] * cnt[1] * cnt[2];
-    if (lane == 0) {
-        PRec pr;
-        const double gfac = 1.0 - 1.0 / in.ratio[p];
-        for (int d = 0; d < 3; ++d) {
-            const double X = in.X[3 * p + d];
-            pr.X[d] = X;
-            const double fl = d < D ? floor(X) : 0.0;
-            pr.ref[d] = (int)fl;
-            pr.frac[d] = (float)(X - fl);
-            pr.a[d] = (float)(gfac * (double)in.ggrav[d] + in.A[3 * p + d]);
-        }
-        pr.R2 = R * R;
-        pr.R2lo = (float)(pr.R2 * (1.0 - 1e-5) - 1e-4);
-        pr.R2hi = (float)(pr.R2 * (1.0 + 1e-5) + 1e-4);
-        pr.ntiles = nt;
-        pr.pad = 0;
-        in.prec[p] = pr;
-        if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
-    }
+    pr.R2 = R * R;
+    const float R2f = Rf * Rf;
+    pr.R2lo = R2f * (1.0f - 2e-5f) - 2e-4f;
+    pr.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
+    pr.ntiles = nt;
+    pr.pad = 0;
+    in.prec[p] = pr;
+    if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
+}
+
+// List entries of particle p in the tiles of its bounding box (lanes share).
+__device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int lpar, int lane,
+                             int nl) {
+    const int cnt[3] = {at[0].na + at[0].nb, at[1].na + at[1].nb, at[2].na + at[2].nb};
+    const int nt = cnt[0] * cnt[1] * cnt[2];
     for (int k = lane; k < nt && k < in.maxk; k += nl) {
         const int kx = k % cnt[0], ky = (k / cnt[0]) % cnt[1], kz = k / (cnt[0] * cnt[1]);
         const int tc[3] = {axis_tile(at[0], kx), axis_tile(at[1], ky), axis_tile(at[2], kz)};
@@ -338,34 +220,43 @@ __device__ void publish_particle(const InstDesc& in, int p, int lpar, int D, con
 }
 
 // Algorithm 1 for particle i (one thread): wall forces, the corrected
-// position, and on the last sub-step A^{n+1}, theta^{n+1} and U^{n-1} <- U^n.
-__device__ void update_particle(const InstDesc& in, int i, int t, const double (*sF)[6], int src,
-                                double h, int last, int D) {
+// position, and on the last sub-step A^{n+1}, theta^{n+1}, U^{n-1} <- U^n
+// and the record for the next step.
+__device__ void update_particle(const InstDesc& in, int i, const double* F1in, const double* F2in,
+                                int src, double h, int last, int D, const Shape& sh, AxisTiles* at) {
     const int dst = src ^ 1;
     const double* Xs = in.Xk + (long long)src * in.np * 3;
-    double X0[3], Xst[3], F1[3], F2[3];
+    // operands up front: their loads overlap instead of following the FP64 chain
+    double X0[3], Ub[3], Xold[3], F1[3], F2[3];
     for (int d = 0; d < 3; ++d) {
         X0[d] = Xs[3 * i + d];
-        Xst[d] = X0[d] + h * in.Ubar[3 * i + d];
-        F1[d] = sF[t][d];
-        F2[d] = sF[t][3 + d];
+        Ub[d] = in.Ubar[3 * i + d];
+        Xold[d] = in.X[3 * i + d];
+        F1[d] = F1in[d];
+        F2[d] = F2in[d];
     }
+    const double invM = in.pconst[PCONST_N * i + PC_INVRHOS] * in.invc[i];  // 1 / (rho_s n)
+    double Xst[3];
+    for (int d = 0; d < 3; ++d) Xst[d] = fma(h, Ub[d], X0[d]);
     wall_force(in, i, X0, F1);
     wall_force(in, i, Xst, F2);
-    const double M = in.ratio[i] * in.rho_f * (double)in.count[i];
+    const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
     double Xn[3];
-    for (int d = 0; d < 3; ++d) Xn[d] = Xst[d] + 1.0 / (2.0 * M) * h * h * 0.5 * (F1[d] + F2[d]);
+    for (int d = 0; d < 3; ++d) Xn[d] = Xst[d] + c * (F1[d] + F2[d]);
     if (!last) {
         double* Xd = in.Xk + (long long)dst * in.np * 3;
         for (int d = 0; d < 3; ++d) Xd[3 * i + d] = Xn[d];
+        const float Rf = (float)in.pconst[PCONST_N * i + PC_R];
         reinterpret_cast<float4*>(in.Xf)[(long long)dst * in.np + i] =
-            make_float4((float)Xn[0], (float)Xn[1], (float)Xn[2], (float)in.R[i]);
+            make_float4((float)Xn[0], (float)Xn[1], (float)Xn[2], Rf);
+        reinterpret_cast<float4*>(in.Xsf)[(long long)dst * in.np + i] =
+            make_float4((float)fma(h, Ub[0], Xn[0]), (float)fma(h, Ub[1], Xn[1]), (float)fma(h, Ub[2], Xn[2]), Rf);
         return;
     }
     bool left = false;
     for (int d = 0; d < 3; ++d) {
         const int j = 3 * i + d;
-        in.A[j] = 2.0 * (Xn[d] - in.X[j] - in.Ubar[j]);
+        in.A[j] = 2.0 * (Xn[d] - Xold[d] - Ub[d]);
         double xn = Xn[d];
         if (d < D) {
             if (in.periodic[d]) {
@@ -376,38 +267,119 @@ __device__ void update_particle(const InstDesc& in, int i, int t, const double (
             }
         }
         in.X[j] = xn;
-        in.theta[j] += 0.5 * (in.Wn[j] + in.W[j]);
-        in.U[j] = in.Un[j];
-        in.W[j] = in.Wn[j];
+        const double wn = in.Wn[j], un = in.Un[j];
+        in.theta[j] += 0.5 * (wn + in.W[j]);
+        in.U[j] = un;
+        in.W[j] = wn;
     }
     if (left) atomicOr(in.status, ST_PARTICLE);
+    make_record(in, i, D, sh, at);
 }
 
-// One sub-step k of Algorithm 1 (positions Xk[src] -> Xk[src ^ 1]) for 32
-// particles per block: the block's warps find the pair forces (4 particles
-// each), one thread per particle does the FP64 update, and after the last
-// sub-step the warps publish the particles for the next fluid step.
-__global__ void __launch_bounds__(256) k_substep(const InstDesc* __restrict__ insts,
-                                                 const PartRef* __restrict__ refs, int ntotal, int D,
-                                                 int src, int K, int last, int lpar, Shape sh) {
-    __shared__ double sF[PB][6];
-    __shared__ float4 xs[XCHUNK];
+// ------------------------------------------------------------- the kernel --
+constexpr unsigned long long PWAIT_NS = 2000000000ull;  // 2 s bound on a barrier wait
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier over all blocks of the particle kernel (launched only when they are
+// all resident).  Bounded: after PWAIT_NS it records a timeout and returns
+// false, and the kernel stops.
+__device__ bool grid_sync(GridBar* gb, int* status) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &gb->gen;
+        const unsigned g = *vgen;  // generation before this block arrives
+        __threadfence();
+        if (atomicAdd(&gb->count, 1) == gridDim.x - 1) {
+            gb->count = 0;
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            while (*vgen == g) {
+                if (gtimer() - t0 > PWAIT_NS) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Phase 0: the rigid-body projection (Eq. 22) of the block's 8 particles.
+// Warp t sums the exact integer slots of particle t (lanes over slots,
+// clearing them for the next step); one thread per particle does the FP64 part.
+__device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
+                               long long (*tot)[NPV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gp0 = blockIdx.x * PB;
-    const int inst = refs[gp0].inst;  // blocks never straddle instances
-    const InstDesc& in = insts[inst];
-    const double h = 1.0 / K;
+    const int gp = gp0 + warp;
+    if (warp < PB && gp < ntotal && refs[gp].inst >= 0) {
+        const int p = refs[gp].p;
+        const int nt = min(in.prec[p].ntiles, in.maxk);  // overflow is flagged at publish
+        long long v[NPV];
+#pragma unroll
+        for (int k = 0; k < NPV; ++k) v[k] = 0;
+        for (int s = lane; s < nt; s += 32) {
+            longlong2* src = reinterpret_cast<longlong2*>(in.partial + ((long long)p * in.maxk + s) * NPV);
+#pragma unroll
+            for (int k = 0; k < NPV / 2; ++k) {
+                const longlong2 a = __ldcg(src + k);
+                v[2 * k] += a.x;
+                v[2 * k + 1] += a.y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NPV; ++k) {
+            const long long w = warp_sum_ll(v[k]);
+            if (lane == 0) tot[warp][k] = w;
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < PB && gp0 + lane < ntotal && refs[gp0 + lane].inst >= 0) {
+        if (D == 2) finalize_particle<2>(in, refs[gp0 + lane].p, tot[lane]);
+        else finalize_particle<3>(in, refs[gp0 + lane].p, tot[lane]);
+    }
+}
+
+// Phase k (1..K): sub-step k of Algorithm 1, positions Xk[src] -> Xk[src ^ 1];
+// the block's warps find the pair forces (one particle each), one thread per
+// particle does the FP64 update.
+__device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
+                              int src, int K, int last, const Shape& sh, float4* xs, float4* xs2,
+                              double (*sF)[6], AxisTiles (*sAT)[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double h = in.hK;
     const int gp = gp0 + warp;
     const bool mine = warp < PB && gp < ntotal && refs[gp].inst >= 0;
     const int i = mine ? refs[gp].p : 0;
     double f1[3] = {0, 0, 0}, f2[3] = {0, 0, 0};
+    if (src == 0 && mine) {  // the projection read this step's slots: clear them for the next
+        const int nt = min(in.prec[i].ntiles, in.maxk);
+        for (int s = lane; s < nt; s += 32) {
+            longlong2* dst = reinterpret_cast<longlong2*>(in.partial + ((long long)i * in.maxk + s) * NPV);
+#pragma unroll
+            for (int k = 0; k < NPV / 2; ++k) dst[k] = make_longlong2(0, 0);
+        }
+    }
     const float4* Xfb = reinterpret_cast<const float4*>(in.Xf) + (long long)src * in.np;
+    const float4* Xsb = reinterpret_cast<const float4*>(in.Xsf) + (long long)src * in.np;
     for (int j0 = 0; j0 < in.np; j0 += XCHUNK) {
         const int nj = min(XCHUNK, in.np - j0);
         __syncthreads();
-        for (int k = threadIdx.x; k < nj; k += blockDim.x) xs[k] = Xfb[j0 + k];
+        for (int k = threadIdx.x; k < nj; k += blockDim.x) {
+            xs[k] = Xfb[j0 + k];
+            xs2[k] = Xsb[j0 + k];
+        }
         __syncthreads();
-        if (mine) pair_chunk(in, i, src, h, lane, xs, j0, nj, f1, f2);
+        if (mine) pair_chunk(in, i, src, h, lane, xs, xs2, j0, nj, f1, f2);
     }
     if (mine) {
         double F1[3], F2[3];
@@ -420,10 +392,37 @@ __global__ void __launch_bounds__(256) k_substep(const InstDesc* __restrict__ in
     }
     __syncthreads();
     if (warp == 0 && lane < PB && gp0 + lane < ntotal && refs[gp0 + lane].inst >= 0)
-        update_particle(in, refs[gp0 + lane].p, lane, sF, src, h, last, D);
-    if (!last) return;
-    __syncthreads();  // new X and A of the block's particles are visible to all warps
-    if (mine) publish_particle(in, i, lpar, D, sh, lane, 32);
+        update_particle(in, refs[gp0 + lane].p, sF[lane], sF[lane] + 3, src, h, last, D, sh, sAT[lane]);
+}
+
+// Particle part of one time step for the block's 8 particles (one instance),
+// phases first..last: 0 = projection, k = sub-step k of Algorithm 1; after the
+// last sub-step the warps append their particle to the next step's tile
+// lists.  With more than one phase the blocks meet at grid barriers between
+// phases (the launch guarantees they are all resident).
+__global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ insts,
+                                                   const PartRef* __restrict__ refs, int ntotal,
+                                                   int D, int K, int first, int last, int lpar,
+                                                   Shape sh, GridBar* gb) {
+    __shared__ long long tot[PB][NPV];
+    __shared__ double sF[PB][6];
+    __shared__ AxisTiles sAT[PB][3];
+    __shared__ float4 xs[XCHUNK];
+    __shared__ float4 xs2[XCHUNK];
+    const int gp0 = blockIdx.x * PB;
+    const InstDesc& in = insts[refs[gp0].inst];  // blocks never straddle instances
+    for (int ph = first; ph <= last; ++ph) {
+        if (ph > first && !grid_sync(gb, in.status)) return;
+        if (ph == 0) phase_finalize(in, refs, ntotal, D, gp0, tot);
+        else phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == K, sh, xs, xs2, sF, sAT);
+    }
+    if (last == K) {
+        __syncthreads();  // records and tile ranges of the block's particles are ready
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int gp = gp0 + warp;
+        if (warp < PB && gp < ntotal && refs[gp].inst >= 0)
+            append_tiles(in, refs[gp].p, sAT[warp], lpar, lane, 32);
+    }
 }
 
 // Publish every particle from its current state (after creation, particle
@@ -434,18 +433,28 @@ __global__ void k_publish(const InstDesc* __restrict__ insts, const PartRef* __r
     if (gp >= ntotal) return;
     const PartRef r = refs[gp];
     if (r.inst < 0) return;
-    publish_particle(insts[r.inst], r.p, lpar, D, sh, 0, 1);
+    AxisTiles at[3];
+    make_record(insts[r.inst], r.p, D, sh, at);
+    append_tiles(insts[r.inst], r.p, at, lpar, 0, 1);
 }
 
-cudaError_t launch_finalize(const InstDesc* insts, const PartRef* refs, int ntotal, int D,
-                            cudaStream_t st) {
-    k_finalize<<<(ntotal + PB - 1) / PB, 256, 0, st>>>(insts, refs, ntotal, D);
-    return cudaGetLastError();
+int particle_blocks_resident(int num_sms) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_particles, 256, 0) != cudaSuccess) return 0;
+    return nb * num_sms;
 }
 
-cudaError_t launch_substep(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int src,
-                           int K, int last, int lpar, const Shape& sh, cudaStream_t st) {
-    k_substep<<<(ntotal + PB - 1) / PB, 256, 0, st>>>(insts, refs, ntotal, D, src, K, last, lpar, sh);
+// The particle part of a step: one launch with grid barriers when all blocks
+// fit on the GPU at once, else one launch per phase.
+cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int K,
+                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st) {
+    const int blocks = (ntotal + PB - 1) / PB;
+    if (fused) {
+        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, 0, K, lpar, sh, gb);
+        return cudaGetLastError();
+    }
+    for (int ph = 0; ph <= K; ++ph)
+        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, ph, ph, lpar, sh, gb);
     return cudaGetLastError();
 }
 
