@@ -216,6 +216,46 @@ int lbm_rigid_projection_noalloc(int dim, const int* n, const int* periodic, con
                                  const double* pos, const double* radius, double max_radius,
                                  double* vel, double* omega, int* count, void* stream);
 
+/* Discrete adjoint (reverse mode) of nsteps time steps, for gradients of a
+ * scalar J of the final state with respect to the density ratios, the
+ * penalty coefficient alpha (Eq. 17), the initial particle state and the
+ * initial populations.  The solid indicator (Eq. 9) is piecewise constant in
+ * the positions and is held fixed: the gradients are those of the recorded
+ * sequence of solid domains.
+ *
+ * lbm_adjoint_forward runs nsteps steps like lbm_step (the context advances)
+ * and keeps checkpoints: the populations and particle state at the start of
+ * each segment of seg_len steps (seg_len = 0: ceil(sqrt(nsteps))).  Device
+ * memory: ceil(nsteps / seg_len) population buffers per instance.
+ *
+ * lbm_adjoint_backward recomputes each segment from its checkpoint, last
+ * segment first (seg_len + 1 more population buffers per instance), and
+ * sweeps backwards through it.  Any call that changes the state (lbm_step,
+ * lbm_set_populations, lbm_load_state, lbm_add_particles) between the two
+ * voids the recording: backward then returns LBM_ERR_STATE.  On return the
+ * context holds the state after the forward pass again.
+ *   seed_particles  host, nullable: dJ/d(final particle state), per instance
+ *                   in instance order, per particle 15 doubles
+ *                   X[3] U[3] W[3] theta[3] A[3] (2D: x, y used; W and theta
+ *                   in the third component);
+ *   seed_field      device, nullable: dJ/d(final populations), per instance
+ *                   Q * N floats in the layout of lbm_get_populations;
+ *   grad_particles  host out: per instance 1 + 16 * np doubles:
+ *                   dJ/dalpha, then per particle dJ/dratio and dJ/d of the
+ *                   initial X[3] U[3] W[3] theta[3] A[3] (U = U^{-1}, the
+ *                   velocity entering the first step);
+ *   grad_field      device out, nullable: dJ/d(initial populations), same
+ *                   layout as seed_field (rest population 0).
+ * The work is issued on the context stream; the call returns after it. */
+int lbm_adjoint_forward(lbm_ctx* ctx, int nsteps, int seg_len);
+int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float* seed_field,
+                         double* grad_particles, float* grad_field);
+/* Both in one call. */
+int lbm_adjoint_run(lbm_ctx* ctx, int nsteps, int seg_len, const double* seed_particles,
+                    const float* seed_field, double* grad_particles, float* grad_field);
+/* Free the adjoint's checkpoints and records (also done by lbm_destroy). */
+int lbm_adjoint_release(lbm_ctx* ctx);
+
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(int status);
 void lbm_destroy(lbm_ctx* ctx);

@@ -37,6 +37,17 @@ int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages);
 cudaError_t launch_fluid_tma(int Q, int fp16, const InstDesc* insts, const void* tmaps,
                              const uint16_t* tile_inst, int ntiles, int par, const Shape& sh,
                              int commit, int grid, int* tile_ctr, int stages, cudaStream_t st);
+cudaError_t launch_adj_fluid(int Q, int fp16, const InstDesc* insts, const AdjFluid* afs,
+                             const uint16_t* tile_inst, int ntiles, int lam_mode, const Shape& sh,
+                             cudaStream_t st);
+cudaError_t launch_adj_particles(int D, const InstDesc* insts, const AdjPart* steps, const AdjBufs* bufs,
+                                 int ninst, cudaStream_t st);
+cudaError_t launch_adj_finish(const InstDesc* insts, const AdjBufs* bufs, const long long* out_off,
+                              double* out, int ninst, cudaStream_t st);
+cudaError_t launch_adj_pull_out(int Q, const InstDesc* insts, int inst, long long N, const float* lam,
+                                float* out, cudaStream_t st);
+cudaError_t launch_adj_state(const InstDesc* insts, int inst, int np, double* rec, int to_record,
+                             cudaStream_t st);
 }  // namespace lbmpen
 
 using namespace lbmpen;
@@ -63,6 +74,23 @@ struct Instance {
     std::vector<double> hratio;  // density ratios (per-particle constants)
 };
 
+// Adjoint recording of one instance: checkpoints of the forward pass and the
+// per-step records of the segment being recomputed.
+struct AdjInst {
+    std::vector<DevBuf> ckpt;   // [nseg] populations at the start of each segment
+    DevBuf ckst;                // [nseg + 1][np][16] particle state at segment starts, then the final one
+    std::vector<DevBuf> slot;   // [L + 1] populations entering each step of the segment
+    DevBuf rprec, rlcnt, rlent, rgeo, rstate;  // [L + 1] records of each step
+    DevBuf fbar[2];             // adjoint of the pre-collision populations (ping-pong)
+    DevBuf pbuf;                // adjoint particle arrays (AdjBufs)
+};
+struct AdjCtx {
+    bool ready = false;         // a recorded forward pass matches the current state
+    int nsteps = 0, L = 0, nseg = 0;
+    std::vector<AdjInst> ai;
+    DevBuf d_rdesc, d_rtmaps, d_afl, d_apt, d_abufs, d_out, d_out_off;
+};
+
 }  // namespace
 
 struct lbm_ctx {
@@ -83,6 +111,7 @@ struct lbm_ctx {
     bool graph_ok[2] = {false, false};
     bool failed = false;
     std::string err;
+    AdjCtx adj;
 };
 
 namespace {
@@ -230,6 +259,7 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.f[0] = I.f[0].ptr;
     d.f[1] = I.f[1].ptr;
     d.prec = P<PRec>(I.prec);
+    d.prec_out = d.prec;
     d.list_cnt[0] = P<int>(I.lcnt[0]);
     d.list_cnt[1] = P<int>(I.lcnt[1]);
     d.list_ent[0] = P<uint32_t>(I.lent[0]);
@@ -260,6 +290,8 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.K = c.K;
     d.hK = 1.0 / c.K;
     d.status = P<int>(ctx->d_status);
+    d.adj_geo = nullptr;
+    d.rec_state = nullptr;
     return d;
 }
 
@@ -343,48 +375,51 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// One tensor map per instance and population buffer: the stored populations
-// as a [Q-1][nz][ny][pitch] tensor (x innermost, dim = nx so that boxes read
+// Tensor map of one population buffer: the stored populations as a
+// [Q-1][nz][ny][pitch] tensor (x innermost, dim = nx so that boxes read
 // zeros beyond the last node), boxes of (tile width + 2 halo) x ty (x tz).
-int build_tmaps(lbm_ctx* ctx) {
+int encode_pop_map(lbm_ctx* ctx, const Instance& I, void* ptr, CUtensorMap* out) {
     auto enc = tmap_encoder();
     if (!enc) return set_err(ctx, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available%s");
     const size_t ss = ctx->fp16 ? 2 : 4;
     const int halo = 16 / (int)ss;
-    std::vector<CUtensorMap> maps(2 * ctx->inst.size());
-    for (size_t i = 0; i < ctx->inst.size(); ++i) {
-        Instance& I = ctx->inst[i];
-        for (int b = 0; b < 2; ++b) {
-            cuuint64_t dims[4], strides[3];
-            cuuint32_t box[4], es[4] = {1, 1, 1, 1};
-            cuuint32_t rank;
-            dims[0] = (cuuint64_t)I.n[0];
-            dims[1] = (cuuint64_t)I.n[1];
-            strides[0] = (cuuint64_t)I.pitch * ss;
-            box[0] = (cuuint32_t)(ctx->shape.tw + 2 * halo);
-            box[1] = (cuuint32_t)ctx->shape.ty;
-            if (ctx->D == 2) {
-                rank = 3;
-                dims[2] = (cuuint64_t)(ctx->Q - 1);
-                strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
-                box[2] = 1;
-            } else {
-                rank = 4;
-                dims[2] = (cuuint64_t)I.n[2];
-                dims[3] = (cuuint64_t)(ctx->Q - 1);
-                strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
-                strides[2] = (cuuint64_t)I.pitch * I.n[1] * I.n[2] * ss;
-                box[2] = (cuuint32_t)ctx->shape.tz;
-                box[3] = 1;
-            }
-            CUresult r = enc(&maps[2 * i + b],
-                             ctx->fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                             rank, I.f[b].ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return set_err(ctx, LBM_ERR_CUDA, "tensor map encoding failed%s");
-        }
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+    cuuint32_t rank;
+    dims[0] = (cuuint64_t)I.n[0];
+    dims[1] = (cuuint64_t)I.n[1];
+    strides[0] = (cuuint64_t)I.pitch * ss;
+    box[0] = (cuuint32_t)(ctx->shape.tw + 2 * halo);
+    box[1] = (cuuint32_t)ctx->shape.ty;
+    if (ctx->D == 2) {
+        rank = 3;
+        dims[2] = (cuuint64_t)(ctx->Q - 1);
+        strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
+        box[2] = 1;
+    } else {
+        rank = 4;
+        dims[2] = (cuuint64_t)I.n[2];
+        dims[3] = (cuuint64_t)(ctx->Q - 1);
+        strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
+        strides[2] = (cuuint64_t)I.pitch * I.n[1] * I.n[2] * ss;
+        box[2] = (cuuint32_t)ctx->shape.tz;
+        box[3] = 1;
     }
+    CUresult r = enc(out, ctx->fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank,
+                     ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, LBM_ERR_CUDA, "tensor map encoding failed%s");
+    return LBM_OK;
+}
+
+// One tensor map per instance and population buffer.
+int build_tmaps(lbm_ctx* ctx) {
+    std::vector<CUtensorMap> maps(2 * ctx->inst.size());
+    for (size_t i = 0; i < ctx->inst.size(); ++i)
+        for (int b = 0; b < 2; ++b) {
+            int rc = encode_pop_map(ctx, ctx->inst[i], ctx->inst[i].f[b].ptr, &maps[2 * i + b]);
+            if (rc) return rc;
+        }
     int rc = dalloc(ctx, ctx->d_tmaps, sizeof(CUtensorMap) * maps.size());
     if (rc) return rc;
     CK(cudaMemcpy(ctx->d_tmaps.ptr, maps.data(), sizeof(CUtensorMap) * maps.size(),
@@ -502,7 +537,22 @@ int read_status(lbm_ctx* ctx) {
     return set_err(ctx, LBM_ERR_CAPACITY, "a tile overlaps more particles than its list holds%s");
 }
 
+void adj_release(lbm_ctx* ctx) {
+    AdjCtx& A = ctx->adj;
+    for (auto& a : A.ai) {
+        for (auto& b : a.ckpt) dfree(ctx, b);
+        for (auto& b : a.slot) dfree(ctx, b);
+        DevBuf* bufs[] = {&a.ckst, &a.rprec, &a.rlcnt, &a.rlent, &a.rgeo, &a.rstate, &a.fbar[0], &a.fbar[1], &a.pbuf};
+        for (DevBuf* b : bufs) dfree(ctx, *b);
+    }
+    A.ai.clear();
+    DevBuf* bufs[] = {&A.d_rdesc, &A.d_rtmaps, &A.d_afl, &A.d_apt, &A.d_abufs, &A.d_out, &A.d_out_off};
+    for (DevBuf* b : bufs) dfree(ctx, *b);
+    A.ready = false;
+}
+
 void destroy_all(lbm_ctx* ctx) {
+    adj_release(ctx);
     invalidate_graphs(ctx);
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
@@ -663,6 +713,7 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
                       const double* ratio, const double* vel, const double* omega) {
     int rc = check_inst(ctx, i);
     if (rc) return rc;
+    ctx->adj.ready = false;
     if (n < 0 || (n > 0 && (!pos || !radius || !ratio)))
         return set_err(ctx, LBM_ERR_INVALID, "bad particle arrays%s");
     if (n == 0) return LBM_OK;
@@ -723,7 +774,7 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
     return republish(ctx);
 }
 
-int lbm_step(lbm_ctx* ctx, int nsteps) {
+static int step_impl(lbm_ctx* ctx, int nsteps) {
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if (nsteps < 0) return set_err(ctx, LBM_ERR_INVALID, "negative step count%s");
@@ -757,6 +808,11 @@ int lbm_step(lbm_ctx* ctx, int nsteps) {
         }
     }
     return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* ctx, int nsteps) {
+    if (ctx) ctx->adj.ready = false;
+    return step_impl(ctx, nsteps);
 }
 
 int lbm_sync(lbm_ctx* ctx) {
@@ -837,6 +893,7 @@ int lbm_get_particles(lbm_ctx* ctx, int i, double* pos, double* vel, double* ome
 int lbm_set_populations(lbm_ctx* ctx, int i, const float* f, int on_device) {
     int rc = check_inst(ctx, i);
     if (rc) return rc;
+    ctx->adj.ready = false;
     if (!f) return set_err(ctx, LBM_ERR_INVALID, "null population array%s");
     Instance& I = ctx->inst[i];
     const long long N = (long long)I.n[0] * I.n[1] * I.n[2];
@@ -921,6 +978,7 @@ int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes) {
 int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
     int rc = check_ctx(ctx);
     if (rc) return rc;
+    ctx->adj.ready = false;
     if (!buf || bytes < 4 * sizeof(long long)) return LBM_ERR_INVALID;
     const char* r = static_cast<const char*>(buf);
     long long hdr[4];
@@ -1100,6 +1158,310 @@ long long lbm_total_nodes(const lbm_ctx* ctx) {
     long long n = 0;
     for (auto& I : ctx->inst) n += (long long)I.n[0] * I.n[1] * I.n[2];
     return n;
+}
+
+// ------------------------------------------------------------- adjoint ---
+// Forward pass with checkpoints: the populations and particle state at the
+// start of every segment of L steps (L = ceil(sqrt(nsteps)) by default), and
+// the final particle state.  The context advances by nsteps like lbm_step.
+int lbm_adjoint_forward(lbm_ctx* ctx, int nsteps, int seg_len) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (nsteps < 1) return set_err(ctx, LBM_ERR_INVALID, "nsteps must be positive%s");
+    if (seg_len < 0) return set_err(ctx, LBM_ERR_INVALID, "negative segment length%s");
+    AdjCtx& A = ctx->adj;
+    A.ready = false;
+    const int L = seg_len > 0 ? std::min(seg_len, nsteps) : std::max(1, (int)ceil(sqrt((double)nsteps)));
+    const int nseg = (nsteps + L - 1) / L;
+    const size_t ssz = ctx->fp16 ? 2 : 4;
+    const int ni = (int)ctx->inst.size();
+    if ((int)A.ai.size() != ni) {
+        adj_release(ctx);
+        A.ai.resize(ni);
+    }
+    for (int i = 0; i < ni; ++i) {
+        Instance& I = ctx->inst[i];
+        AdjInst& a = A.ai[i];
+        const size_t fb = ssz * (size_t)(ctx->Q - 1) * (size_t)I.qstride;
+        for (size_t s = nseg; s < a.ckpt.size(); ++s) dfree(ctx, a.ckpt[s]);
+        a.ckpt.resize(nseg);
+        for (int s = 0; s < nseg; ++s)
+            if ((rc = dalloc(ctx, a.ckpt[s], fb))) return rc;
+        if ((rc = dalloc(ctx, a.ckst, sizeof(double) * 16 * (size_t)std::max(I.np, 1) * (nseg + 1)))) return rc;
+    }
+    for (int s = 0; s < nseg; ++s) {
+        for (int i = 0; i < ni; ++i) {
+            Instance& I = ctx->inst[i];
+            AdjInst& a = A.ai[i];
+            CK(cudaMemcpyAsync(a.ckpt[s].ptr, I.f[ctx->par].ptr, a.ckpt[s].bytes, cudaMemcpyDeviceToDevice,
+                               ctx->st));
+            CK(launch_adj_state(P<InstDesc>(ctx->d_insts), i, I.np, P<double>(a.ckst) + 16LL * I.np * s, 1,
+                                ctx->st));
+        }
+        if ((rc = step_impl(ctx, std::min(L, nsteps - s * L)))) return rc;
+    }
+    for (int i = 0; i < ni; ++i) {
+        Instance& I = ctx->inst[i];
+        CK(launch_adj_state(P<InstDesc>(ctx->d_insts), i, I.np, P<double>(A.ai[i].ckst) + 16LL * I.np * nseg,
+                            1, ctx->st));
+    }
+    A.nsteps = nsteps;
+    A.L = L;
+    A.nseg = nseg;
+    A.ready = true;
+    return LBM_OK;
+}
+
+namespace {
+
+// Adjoint particle arrays of one instance inside one allocation.
+size_t adj_pbuf_doubles(int np, int K) {
+    const size_t n3 = 3 * (size_t)std::max(np, 1);
+    return 5 * n3 + (size_t)std::max(np, 1) + 1 + 4 * (size_t)std::max(np, 1) + 4 * (size_t)std::max(np, 1) +
+           n3 + (size_t)(K + 1) * n3 + 3 * (size_t)K * n3 + 5 * n3 + 8;
+}
+AdjBufs adj_bufs_layout(void* base, int np, int K) {
+    double* q = static_cast<double*>(base);
+    const size_t n1 = (size_t)std::max(np, 1), n3 = 3 * n1;
+    AdjBufs b;
+    b.Xb = q; q += n3;
+    b.Ub = q; q += n3;
+    b.Wb = q; q += n3;
+    b.Tb = q; q += n3;
+    b.Ab = q; q += n3;
+    b.rb = q; q += n1;
+    b.alpha_b = q; q += 1;
+    b.Abar = q; q += 4 * n1;
+    b.coef = reinterpret_cast<float*>(q); q += 4 * n1;
+    b.Ubar = q; q += n3;
+    b.Xk = q; q += (size_t)(K + 1) * n3;
+    b.Xs = q; q += (size_t)K * n3;
+    b.F1 = q; q += (size_t)K * n3;
+    b.F2 = q; q += (size_t)K * n3;
+    b.Xkb = q; q += n3;
+    b.Xsb = q; q += n3;
+    b.v = q; q += n3;
+    b.Ubb = q; q += n3;
+    b.Wnb = q; q += n3;
+    return b;
+}
+
+}  // namespace
+
+// Backward sweep over the recorded forward pass (see lbmpen.h for layouts).
+int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float* seed_field,
+                         double* grad_particles, float* grad_field) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    AdjCtx& A = ctx->adj;
+    if (!A.ready) return set_err(ctx, LBM_ERR_STATE, "no recorded forward pass (call lbm_adjoint_forward)%s");
+    if (!grad_particles) return set_err(ctx, LBM_ERR_INVALID, "null gradient array%s");
+    const int ni = (int)ctx->inst.size(), L = A.L, nseg = A.nseg, N = A.nsteps;
+    const int K = ctx->inst[0].cfg.K;
+    const size_t ssz = ctx->fp16 ? 2 : 4;
+    const Shape& sh = ctx->shape;
+    // records, slots and adjoint arrays
+    for (int i = 0; i < ni; ++i) {
+        Instance& I = ctx->inst[i];
+        AdjInst& a = A.ai[i];
+        const size_t n1 = (size_t)std::max(I.np, 1);
+        const size_t fb = ssz * (size_t)(ctx->Q - 1) * (size_t)I.qstride;
+        for (size_t k = L + 1; k < a.slot.size(); ++k) dfree(ctx, a.slot[k]);
+        a.slot.resize(L + 1);
+        for (int k = 0; k <= L; ++k)
+            if ((rc = dalloc(ctx, a.slot[k], fb))) return rc;
+        if ((rc = dalloc(ctx, a.rprec, sizeof(PRec) * n1 * (L + 1))) ||
+            (rc = dalloc(ctx, a.rlcnt, sizeof(int) * (size_t)I.ntiles * (L + 1))) ||
+            (rc = dalloc(ctx, a.rlent, sizeof(uint32_t) * (size_t)I.ntiles * LIST_CAP * (L + 1))) ||
+            (rc = dalloc(ctx, a.rgeo, sizeof(double) * NPV * n1 * (L + 1))) ||
+            (rc = dalloc(ctx, a.rstate, sizeof(double) * 16 * n1 * (L + 1))) ||
+            (rc = dalloc(ctx, a.fbar[0], sizeof(float) * (ctx->Q - 1) * (size_t)I.qstride)) ||
+            (rc = dalloc(ctx, a.fbar[1], sizeof(float) * (ctx->Q - 1) * (size_t)I.qstride)) ||
+            (rc = dalloc(ctx, a.pbuf, sizeof(double) * adj_pbuf_doubles(I.np, K))))
+            return rc;
+        CK(cudaMemsetAsync(a.pbuf.ptr, 0, a.pbuf.bytes, ctx->st));
+    }
+    // descriptors of the recomputation: step k reads slot k and writes slot
+    // k + 1, its records go to record k (and k + 1 for the next step's input);
+    // entry L is the publish of a segment's first state into record 0
+    std::vector<InstDesc> rd((size_t)(L + 1) * ni);
+    std::vector<CUtensorMap> tm(sh.tma ? (size_t)L * ni * 2 : 0);
+    for (int k = 0; k <= L; ++k)
+        for (int i = 0; i < ni; ++i) {
+            Instance& I = ctx->inst[i];
+            AdjInst& a = A.ai[i];
+            const size_t n1 = (size_t)std::max(I.np, 1);
+            InstDesc d = make_desc(ctx, I);
+            PRec* rp = P<PRec>(a.rprec);
+            int* lc = P<int>(a.rlcnt);
+            uint32_t* le = P<uint32_t>(a.rlent);
+            if (k == L) {
+                d.prec_out = rp;
+                d.list_cnt[0] = lc;
+                d.list_ent[0] = le;
+            } else {
+                const int par = k & 1;
+                d.f[par] = a.slot[k].ptr;
+                d.f[par ^ 1] = a.slot[k + 1].ptr;
+                d.prec = rp + n1 * k;
+                d.prec_out = rp + n1 * (k + 1);
+                d.list_cnt[par] = lc + (size_t)I.ntiles * k;
+                d.list_ent[par] = le + (size_t)I.ntiles * LIST_CAP * k;
+                d.list_cnt[par ^ 1] = lc + (size_t)I.ntiles * (k + 1);
+                d.list_ent[par ^ 1] = le + (size_t)I.ntiles * LIST_CAP * (k + 1);
+                d.adj_geo = P<double>(a.rgeo) + NPV * n1 * k;
+                d.rec_state = P<double>(a.rstate) + 16 * n1 * (k + 1);
+                if (sh.tma) {
+                    if ((rc = encode_pop_map(ctx, I, a.slot[k].ptr, &tm[(size_t)k * ni * 2 + 2 * i + par]))) return rc;
+                    if ((rc = encode_pop_map(ctx, I, a.slot[k + 1].ptr, &tm[(size_t)k * ni * 2 + 2 * i + (par ^ 1)])))
+                        return rc;
+                }
+            }
+            rd[(size_t)k * ni + i] = d;
+        }
+    if ((rc = dalloc(ctx, A.d_rdesc, sizeof(InstDesc) * rd.size()))) return rc;
+    CK(cudaMemcpyAsync(A.d_rdesc.ptr, rd.data(), sizeof(InstDesc) * rd.size(), cudaMemcpyHostToDevice, ctx->st));
+    if (sh.tma) {
+        if ((rc = dalloc(ctx, A.d_rtmaps, sizeof(CUtensorMap) * tm.size()))) return rc;
+        CK(cudaMemcpyAsync(A.d_rtmaps.ptr, tm.data(), sizeof(CUtensorMap) * tm.size(), cudaMemcpyHostToDevice,
+                           ctx->st));
+    }
+    // per-step views of the backward sweep, for every global step
+    std::vector<AdjFluid> afl((size_t)N * ni);
+    std::vector<AdjPart> apt((size_t)N * ni);
+    std::vector<AdjBufs> ab(ni);
+    std::vector<long long> out_off(ni);
+    long long nout = 0;
+    long long foff = 0;
+    std::vector<long long> field_off(ni);
+    for (int i = 0; i < ni; ++i) {
+        Instance& I = ctx->inst[i];
+        ab[i] = adj_bufs_layout(A.ai[i].pbuf.ptr, I.np, K);
+        out_off[i] = nout;
+        nout += 1 + 16LL * I.np;
+        field_off[i] = foff;
+        foff += (long long)ctx->Q * I.n[0] * I.n[1] * I.n[2];
+    }
+    for (int n = 0; n < N; ++n) {
+        const int k = n % L;
+        for (int i = 0; i < ni; ++i) {
+            Instance& I = ctx->inst[i];
+            AdjInst& a = A.ai[i];
+            const size_t n1 = (size_t)std::max(I.np, 1);
+            AdjFluid f;
+            f.fin = a.slot[k].ptr;
+            f.prec = P<PRec>(a.rprec) + n1 * k;
+            f.lcnt = P<int>(a.rlcnt) + (size_t)I.ntiles * k;
+            f.lent = P<uint32_t>(a.rlent) + (size_t)I.ntiles * LIST_CAP * k;
+            f.lam_src = (n == N - 1) ? (seed_field ? seed_field + field_off[i] : nullptr) : P<float>(a.fbar[(n + 1) & 1]);
+            f.lam_dst = P<float>(a.fbar[n & 1]);
+            f.coef = ab[i].coef;
+            f.Abar = ab[i].Abar;
+            afl[(size_t)n * ni + i] = f;
+            AdjPart pp;
+            pp.st0 = P<double>(a.rstate) + 16 * n1 * k;
+            pp.st1 = P<double>(a.rstate) + 16 * n1 * (k + 1);
+            pp.geo = P<double>(a.rgeo) + NPV * n1 * k;
+            apt[(size_t)n * ni + i] = pp;
+        }
+    }
+    if ((rc = dalloc(ctx, A.d_afl, sizeof(AdjFluid) * afl.size())) ||
+        (rc = dalloc(ctx, A.d_apt, sizeof(AdjPart) * apt.size())) ||
+        (rc = dalloc(ctx, A.d_abufs, sizeof(AdjBufs) * ni)) ||
+        (rc = dalloc(ctx, A.d_out, sizeof(double) * std::max<long long>(nout, 1))) ||
+        (rc = dalloc(ctx, A.d_out_off, sizeof(long long) * ni)))
+        return rc;
+    CK(cudaMemcpyAsync(A.d_afl.ptr, afl.data(), sizeof(AdjFluid) * afl.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(A.d_apt.ptr, apt.data(), sizeof(AdjPart) * apt.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(A.d_abufs.ptr, ab.data(), sizeof(AdjBufs) * ni, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(A.d_out_off.ptr, out_off.data(), sizeof(long long) * ni, cudaMemcpyHostToDevice, ctx->st));
+    // seeds: the adjoint of the final particle state
+    std::vector<std::vector<double>> seeds(ni);
+    if (seed_particles) {
+        const double* sp = seed_particles;
+        for (int i = 0; i < ni; ++i) {
+            const int np = ctx->inst[i].np;
+            std::vector<double>& h = seeds[i];
+            h.assign(15 * (size_t)np, 0.0);
+            for (int p = 0; p < np; ++p)
+                for (int a5 = 0; a5 < 5; ++a5)
+                    for (int d = 0; d < 3; ++d) h[(size_t)a5 * 3 * np + 3 * p + d] = sp[15 * p + 3 * a5 + d];
+            if (np) CK(cudaMemcpyAsync(ab[i].Xb, h.data(), sizeof(double) * 15 * np, cudaMemcpyHostToDevice, ctx->st));
+            sp += 15 * (size_t)np;
+        }
+    }
+    const InstDesc* dI = P<InstDesc>(ctx->d_insts);
+    const InstDesc* dR = P<InstDesc>(A.d_rdesc);
+    const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int len = std::min(L, N - s * L);
+        // restore the segment's first state into slot 0, record 0 and the context
+        for (int i = 0; i < ni; ++i) {
+            Instance& I = ctx->inst[i];
+            AdjInst& a = A.ai[i];
+            CK(cudaMemcpyAsync(a.slot[0].ptr, a.ckpt[s].ptr, a.ckpt[s].bytes, cudaMemcpyDeviceToDevice, ctx->st));
+            double* st = P<double>(a.ckst) + 16LL * I.np * s;
+            CK(launch_adj_state(dI, i, I.np, st, 0, ctx->st));
+            if (I.np)
+                CK(cudaMemcpyAsync(a.rstate.ptr, st, sizeof(double) * 16 * I.np, cudaMemcpyDeviceToDevice, ctx->st));
+            CK(cudaMemsetAsync(a.rlcnt.ptr, 0, sizeof(int) * I.ntiles, ctx->st));
+            CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
+        }
+        if (ctx->np_total > 0)
+            CK(launch_publish(dR + (size_t)L * ni, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, 0, sh, ctx->st));
+        // recompute the segment into the slots and records
+        for (int k = 0; k < len; ++k) {
+            const int par = k & 1;
+            const InstDesc* dk = dR + (size_t)k * ni;
+            if (sh.tma)
+                CK(launch_fluid_tma(ctx->Q, ctx->fp16, dk, P<CUtensorMap>(A.d_rtmaps) + (size_t)k * ni * 2,
+                                    P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1, ctx->grid,
+                                    P<int>(ctx->d_tile_ctr), sh.stages, ctx->st));
+            else
+                CK(launch_fluid(ctx->Q, ctx->fp16, dk, P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1,
+                                sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), ctx->st));
+            if (ctx->np_total > 0)
+                CK(launch_particles(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, K, par ^ 1, sh,
+                                    P<GridBar>(ctx->d_gridbar), fused, ctx->st));
+        }
+        // backward through the segment
+        for (int k = len - 1; k >= 0; --k) {
+            const int n = s * L + k;
+            CK(launch_adj_particles(ctx->D, dI, P<AdjPart>(A.d_apt) + (size_t)n * ni, P<AdjBufs>(A.d_abufs), ni,
+                                    ctx->st));
+            const int mode = n == N - 1 ? (seed_field ? 1 : 2) : 0;
+            CK(launch_adj_fluid(ctx->Q, ctx->fp16, dI, P<AdjFluid>(A.d_afl) + (size_t)n * ni,
+                                P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, mode, sh, ctx->st));
+        }
+    }
+    CK(launch_adj_finish(dI, P<AdjBufs>(A.d_abufs), P<long long>(A.d_out_off), P<double>(A.d_out), ni, ctx->st));
+    if (grad_field)
+        for (int i = 0; i < ni; ++i) {
+            Instance& I = ctx->inst[i];
+            const long long Nn = (long long)I.n[0] * I.n[1] * I.n[2];
+            CK(launch_adj_pull_out(ctx->Q, dI, i, Nn, P<float>(A.ai[i].fbar[0]), grad_field + field_off[i], ctx->st));
+        }
+    // the context returns to the state after the forward pass
+    for (int i = 0; i < ni; ++i) {
+        Instance& I = ctx->inst[i];
+        CK(launch_adj_state(dI, i, I.np, P<double>(A.ai[i].ckst) + 16LL * I.np * nseg, 0, ctx->st));
+    }
+    CK(cudaMemcpyAsync(grad_particles, A.d_out.ptr, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->st));
+    return read_status(ctx);
+}
+
+int lbm_adjoint_run(lbm_ctx* ctx, int nsteps, int seg_len, const double* seed_particles, const float* seed_field,
+                    double* grad_particles, float* grad_field) {
+    int rc = lbm_adjoint_forward(ctx, nsteps, seg_len);
+    if (rc) return rc;
+    return lbm_adjoint_backward(ctx, seed_particles, seed_field, grad_particles, grad_field);
+}
+
+int lbm_adjoint_release(lbm_ctx* ctx) {
+    if (!ctx) return LBM_ERR_INVALID;
+    cudaStreamSynchronize(ctx->st);
+    adj_release(ctx);
+    return LBM_OK;
 }
 
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

@@ -589,6 +589,21 @@ __device__ void finalize_particle(const InstDesc& in, int p, const long long* v)
             Wo[col] = dc * idet;
         }
     }
+    if (in.adj_geo) {  // adjoint recording: the sums about X^n that the projection used
+        double* g = in.adj_geo + (long long)NPV * p;
+        const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+        g[0] = cnt;
+        for (int d = 0; d < 3; ++d) g[1 + d] = (double)v[1 + d] - cnt * phi[d];
+        for (int k = 0; k < 6; ++k) {
+            const int i = ii[k], j = jj[k];
+            g[4 + k] = (double)v[4 + k] - phi[i] * (double)v[1 + j] - phi[j] * (double)v[1 + i] +
+                       cnt * phi[i] * phi[j];
+        }
+        for (int d = 0; d < 3; ++d) g[10 + d] = Su[d];
+        g[13] = (double)v[13] * FX_SCALE - (phi[1] * Su[2] - phi[2] * Su[1]);
+        g[14] = (double)v[14] * FX_SCALE - (phi[2] * Su[0] - phi[0] * Su[2]);
+        g[15] = (double)v[15] * FX_SCALE - (phi[0] * Su[1] - phi[1] * Su[0]);
+    }
     bool fast = false;
     float Xs[3] = {0.f, 0.f, 0.f};
 #pragma unroll

@@ -138,7 +138,9 @@ struct InstDesc {
     float s_store, s_load;    // FP16 storage scale 2^k and 2^-k (1 for FP32)
     float wterm[3][2][19];    // bounce-back term 2 w_q (c_q . u_wall) / cs^2 per face
     void* f[2];
-    PRec* prec;               // [np]
+    PRec* prec;               // [np] records read by this step's fluid kernel
+    PRec* prec_out;           // [np] records written for the next step (== prec except
+                              //   while the adjoint recomputes a segment into per-step slots)
     int* list_cnt[2];         // [ntiles]
     uint32_t* list_ent[2];    // [ntiles][LIST_CAP]
     long long* partial;       // [np][maxk][NPV], cleared by the finalize kernel
@@ -167,6 +169,10 @@ struct InstDesc {
     double hK;                // 1 / K
     int K;
     int* status;
+    // adjoint recording (null outside the adjoint's segment recomputation):
+    double* adj_geo;          // [np][NPV] projection sums of this step about X^n: count,
+                              //   sum r (3), sum r r^T (xx yy zz xy xz yz), sum u (3), sum r x u (3)
+    double* rec_state;        // [np][16] state after this step: X, U, W, theta, A (3 each), count
 };
 
 // Kernel shape of the fused fluid kernel: a tile is (32 * vec) x rows_y x rows_z
@@ -179,6 +185,48 @@ struct Shape {
     int tma;     // 1: TMA-staged pipeline kernel
     int stages;  // TMA path: shared-memory ring stages
     int tw;      // tile width in nodes (32 * vec, or the TMA box width without halo)
+};
+
+// ------------------------------------------------------------- adjoint ---
+// One instance's view of one step of the backward sweep (see lbm_adjoint.cu).
+struct AdjFluid {
+    const void* fin;         // populations entering step n (storage type, population layout)
+    const PRec* prec;        // particle records of step n
+    const int* lcnt;         // tile lists of step n
+    const uint32_t* lent;
+    const float* lam_src;    // adjoint of the pre-collision populations of step n + 1
+                             //   (population layout, FP32), or the field seed ([Q][N])
+    float* lam_dst;          // adjoint of the pre-collision populations of step n
+    const float* coef;       // [np][8]: dU^n / count (3), I^-1 dW^n (3)
+    double* Abar;            // [np][4]: sums over the particle's nodes of the adjoint
+                             //   acceleration (3) and of the alpha derivative (1)
+};
+struct AdjPart {
+    const double* st0;       // [np][16] state entering step n
+    const double* st1;       // [np][16] state after step n (U^n, W^n, count^n)
+    const double* geo;       // [np][NPV] projection sums of step n
+};
+// Per-instance adjoint of the particle state and scratch of the particle sweep.
+struct AdjBufs {
+    double* Xb;              // [np][3] adjoint of X entering the current step
+    double* Ub;              // [np][3] ... of U^{n-1}
+    double* Wb;              // [np][3] ... of W^{n-1}
+    double* Tb;              // [np][3] ... of theta
+    double* Ab;              // [np][3] ... of A (seed part; the fluid part is in Abar)
+    double* rb;              // [np]    d J / d ratio
+    double* alpha_b;         // [1]     d J / d alpha
+    double* Abar;            // [np][4] (see AdjFluid)
+    float* coef;             // [np][8]
+    double* Ubar;            // [np][3] scratch: (U^n + U^{n-1}) / 2
+    double* Xk;              // [K+1][np][3] sub-step positions
+    double* Xs;              // [K][np][3] predicted positions
+    double* F1;              // [K][np][3] collision force at Xk (C = 1: per unit C)
+    double* F2;              // [K][np][3] ... at Xs
+    double* Xkb;             // [np][3] adjoint of the current sub-step position
+    double* Xsb;             // [np][3]
+    double* v;               // [np][3] adjoint of the sub-step force sum
+    double* Ubb;             // [np][3] adjoint of Ubar
+    double* Wnb;             // [np][3] adjoint of W^n
 };
 
 // Particle index -> (instance, local index) for the per-particle kernels.

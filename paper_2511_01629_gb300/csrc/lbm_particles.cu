@@ -198,7 +198,7 @@ __device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, A
     pr.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
     pr.ntiles = nt;
     pr.pad = 0;
-    in.prec[p] = pr;
+    in.prec_out[p] = pr;
     if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
 }
 
@@ -273,6 +273,17 @@ __device__ void update_particle(const InstDesc& in, int i, const double* F1in, c
         in.W[j] = wn;
     }
     if (left) atomicOr(in.status, ST_PARTICLE);
+    if (in.rec_state) {  // adjoint recording: the state this step hands to the next
+        double* r = in.rec_state + 16LL * i;
+        for (int d = 0; d < 3; ++d) {
+            r[d] = in.X[3 * i + d];
+            r[3 + d] = in.U[3 * i + d];
+            r[6 + d] = in.W[3 * i + d];
+            r[9 + d] = in.theta[3 * i + d];
+            r[12 + d] = in.A[3 * i + d];
+        }
+        r[15] = (double)in.count[i];
+    }
     make_record(in, i, D, sh, at);
 }
 

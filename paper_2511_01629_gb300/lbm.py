@@ -20,7 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "liblbmpen.so")
-_SOURCES = ["lbm_fluid.cu", "lbm_fluid_tma.cu", "lbm_particles.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+_SOURCES = ["lbm_fluid.cu", "lbm_fluid_tma.cu", "lbm_particles.cu", "lbm_api.cu", "lbm_noalloc.cu",
+            "lbm_adjoint.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC"]
 
@@ -117,6 +118,10 @@ def lib():
         "lbm_fluid_step_only": (C.c_int, [_vp]),
         "lbm_steps_done": (C.c_longlong, [_vp]),
         "lbm_total_nodes": (C.c_longlong, [_vp]),
+        "lbm_adjoint_forward": (C.c_int, [_vp, C.c_int, C.c_int]),
+        "lbm_adjoint_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "lbm_adjoint_run": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
+        "lbm_adjoint_release": (C.c_int, [_vp]),
         "lbm_last_error": (C.c_char_p, [_vp]),
         "lbm_status_string": (C.c_char_p, [C.c_int]),
         "lbm_destroy": (None, [_vp]),
@@ -338,6 +343,61 @@ class LBM:
 
     def fluid_step_only(self):
         self._check(lib().lbm_fluid_step_only(self._h))
+
+    # -- adjoint --
+    def adjoint_forward(self, nsteps: int, seg_len: int = 0):
+        """Run nsteps steps keeping checkpoints for adjoint_backward."""
+        self._check(lib().lbm_adjoint_forward(self._h, int(nsteps), int(seg_len)))
+
+    def adjoint_backward(self, seeds=None, seed_field=None, want_field=False):
+        """Gradients of J = sum(seed * final state) over the recorded steps.
+
+        seeds: per instance a dict with any of X, U, A ([np, D]) and W, theta
+        ([np, 1] in 2D, [np, 3] in 3D); seed_field: a device float32 tensor of
+        Q * N values per instance (instance order), or None.  Returns per
+        instance a dict alpha, ratio [np], X, U, A [np, D], W, theta, and,
+        with want_field, the device tensor dJ / d(initial populations)."""
+        import torch
+        ninst = len(self.configs)
+        nps = [self.num_particles(i) for i in range(ninst)]
+        D = self.D
+        sp = np.zeros(sum(15 * n for n in nps))
+        o = 0
+        for i, n in enumerate(nps):
+            blk = sp[o:o + 15 * n].reshape(n, 15)
+            s = (seeds[i] if seeds is not None else None) or {}
+            for k, c0 in (("X", 0), ("U", 3), ("A", 12)):
+                if k in s:
+                    blk[:, c0:c0 + D] = np.asarray(s[k], np.float64).reshape(n, D)
+            for k, c0 in (("W", 6), ("theta", 9)):
+                if k in s:
+                    v = np.asarray(s[k], np.float64).reshape(n, -1)
+                    if D == 2:
+                        blk[:, c0 + 2] = v[:, 0]
+                    else:
+                        blk[:, c0:c0 + 3] = v
+            o += 15 * n
+        out = np.zeros(sum(1 + 16 * n for n in nps))
+        gfield = None
+        if want_field:
+            total = sum(self.Q * self.nodes(i) for i in range(ninst))
+            gfield = torch.zeros(total, dtype=torch.float32, device="cuda")
+        sf = None if seed_field is None else C.c_void_p(seed_field.data_ptr())
+        self._check(lib().lbm_adjoint_backward(self._h, _ptr(sp), sf, _ptr(out),
+                                               None if gfield is None else C.c_void_p(gfield.data_ptr())))
+        res = []
+        o = 0
+        for n in nps:
+            r = out[o + 1:o + 1 + 16 * n].reshape(n, 16)
+            wcol = [2] if D == 2 else [0, 1, 2]
+            res.append({"alpha": float(out[o]), "ratio": r[:, 0].copy(), "X": r[:, 1:1 + D].copy(),
+                        "U": r[:, 4:4 + D].copy(), "W": r[:, [7 + c for c in wcol]].copy(),
+                        "theta": r[:, [10 + c for c in wcol]].copy(), "A": r[:, 13:13 + D].copy()})
+            o += 1 + 16 * n
+        return (res, gfield) if want_field else res
+
+    def adjoint_release(self):
+        self._check(lib().lbm_adjoint_release(self._h))
 
     @property
     def steps(self) -> int:

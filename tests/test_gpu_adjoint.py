@@ -1,0 +1,229 @@
+"""The hand-written adjoint of the CUDA library (lbm_adjoint_forward/backward)
+against reverse-mode autograd of the FP64 twin of the oracle (oracle/twin.py,
+pinned to the C oracle and to its finite differences), and against central
+finite differences of the C oracle itself.
+
+The forward runs in FP32 on the GPU and in FP64 in the references, so the
+Jacobians are evaluated at states that differ by FP32 rounding; the
+gradients agree to ~1e-6 relative, and the tests ask for 1e-4 (relative to
+the largest entry of each group).  The solid indicator is held fixed by the
+adjoint; each case checks that the GPU and the reference see the same one.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_01629_gb300 import lbm
+
+gpu = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle.twin import Twin  # noqa: E402
+
+F64 = torch.float64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu_setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    lbm.build()
+    yield
+
+
+def _case(D, n, per, pos, R, ratio, K, tau, alpha, g, drive=(1e-5, 0, 0), seed=0, wall_u=None):
+    rng = np.random.default_rng(seed)
+    Q = 9 if D == 2 else 19
+    N = int(np.prod(n))
+    f0 = rng.uniform(-1e-3, 1e-3, (Q, N)).astype(np.float32)
+    f0[0] = 0
+    npart = len(R)
+    U0 = np.zeros((npart, D))
+    U0[:] = rng.uniform(-1e-3, 1e-3, (npart, D))
+    bc = [lbm.LBM_PERIODIC if per[d] else lbm.LBM_WALL for d in range(3)]
+    cfg = lbm.make_config(lattice=Q, n=n, bc=bc, tau=tau, alpha=alpha, g_drive=drive, g_grav=g, K=K,
+                          max_particles=max(npart, 1), max_radius=max(R) + 1, wall_u=wall_u)
+    ocfg = oracle.make_config(D=D, n=n, periodic=per, tau=tau, alpha=alpha, g_drive=drive, g_grav=g, K=K,
+                              wall_u=wall_u)
+    return dict(D=D, Q=Q, N=N, f0=f0, U0=U0, pos=np.asarray(pos, np.float64), R=np.asarray(R, np.float64),
+                ratio=np.asarray(ratio, np.float64), cfg=cfg, ocfg=ocfg, alpha=alpha)
+
+
+def _seeds(c, seed=3):
+    rng = np.random.default_rng(seed)
+    npart, D = len(c["R"]), c["D"]
+    nw = 1 if D == 2 else 3
+    s = {"X": rng.normal(size=(npart, D)), "U": rng.normal(size=(npart, D)) * 10,
+         "W": rng.normal(size=(npart, nw)) * 10, "theta": rng.normal(size=(npart, nw)),
+         "A": rng.normal(size=(npart, D)) * 100}
+    sf = rng.normal(size=(c["Q"], c["N"])).astype(np.float32) * 1e-2
+    sf[0] = 0
+    return s, sf
+
+
+def _gpu_adjoint(c, steps, seg_len, seeds, sfield, ninst=1):
+    sim = lbm.LBM([c["cfg"]] * ninst)
+    for i in range(ninst):
+        sim.set_populations(c["f0"], i)
+        sim.add_particles(i, c["pos"], c["R"], c["ratio"], vel=c["U0"])
+    sim.adjoint_forward(steps, seg_len)
+    sf = torch.tensor(np.tile(sfield.reshape(-1), ninst), device="cuda")
+    res, gf = sim.adjoint_backward([seeds] * ninst, sf, want_field=True)
+    owner = sim.fields(0)[2]
+    parts = sim.particles(0)
+    torch.cuda.synchronize()
+    sim.close()
+    return res, gf.cpu().numpy().reshape(ninst, c["Q"], c["N"]), owner, parts
+
+
+def _twin_grads(c, steps, seeds, sfield):
+    D, npart = c["D"], len(c["R"])
+    X = torch.zeros(npart, 3, dtype=F64)
+    X[:, :D] = torch.tensor(c["pos"])
+    U = torch.zeros(npart, 3, dtype=F64)
+    U[:, :D] = torch.tensor(c["U0"])
+    W = torch.zeros(npart, 3, dtype=F64)
+    T = torch.zeros(npart, 3, dtype=F64)
+    A = torch.zeros(npart, 3, dtype=F64)
+    f = torch.tensor(c["f0"].astype(np.float64))
+    ratio = torch.tensor(c["ratio"])
+    alpha = torch.tensor(c["alpha"], dtype=F64)
+    leaves = [f, X, U, W, T, A, ratio, alpha]
+    for t in leaves:
+        t.requires_grad_(True)
+    out = Twin(c["ocfg"]).run(f, X, U, W, T, A, c["R"], ratio, alpha, steps, keep_owners=True)
+    wcol = [2] if D == 2 else [0, 1, 2]
+    J = (torch.tensor(seeds["X"]) * out["X"][:, :D]).sum() + (torch.tensor(seeds["U"]) * out["U"][:, :D]).sum() \
+        + (torch.tensor(seeds["W"]) * out["W"][:, wcol]).sum() \
+        + (torch.tensor(seeds["theta"]) * out["theta"][:, wcol]).sum() \
+        + (torch.tensor(seeds["A"]) * out["A"][:, :D]).sum() \
+        + (torch.tensor(sfield.astype(np.float64)) * out["f"]).sum()
+    J.backward()
+    g = {"field": f.grad.numpy(), "X": X.grad[:, :D].numpy(), "U": U.grad[:, :D].numpy(),
+         "W": W.grad[:, wcol].numpy(), "theta": T.grad[:, wcol].numpy(), "A": A.grad[:, :D].numpy(),
+         "ratio": ratio.grad.numpy(), "alpha": float(alpha.grad)}
+    return g, out
+
+
+def _close(a, b, rel=1e-4, what=""):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max() / scale
+    assert err <= rel, f"{what}: max rel err {err:.3e} (scale {scale:.3e})"
+
+
+CASES = {
+    # two disks within collision range, K = 2, periodic in x, walls in y
+    "2d": (2, (26, 20, 1), (1, 0, 1), [[8.2, 10.1], [14.1, 9.9]], [3.1, 2.6], [1.5, 1.8], 2, 1.0, 0.8,
+           (0, -1e-4, 0)),
+    # a disk near a wall (wall force) and one in the bulk, closed box
+    "2d-walls": (2, (22, 20, 1), (0, 0, 1), [[3.0, 10.2], [14.8, 6.9]], [3.2, 2.9], [1.6, 1.3], 1, 0.9,
+                 1.0 / 0.9, (0, -1e-4, 0)),
+    "3d": (3, (14, 12, 10), (0, 1, 0), [[5.2, 5.1, 4.8], [9.0, 6.9, 5.3]], [2.6, 2.4], [1.5, 1.3], 2, 1.0, 0.7,
+           (0, 0, -1e-4)),
+}
+
+
+@gpu
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_matches_autograd_twin(name):
+    D, n, per, pos, R, ratio, K, tau, alpha, g = CASES[name]
+    c = _case(D, n, per, pos, R, ratio, K, tau, alpha, g, seed=list(CASES).index(name))
+    steps = 12
+    seeds, sfield = _seeds(c)
+    res, gf, owner, parts = _gpu_adjoint(c, steps, 5, seeds, sfield)
+    ref, out = _twin_grads(c, steps, seeds, sfield)
+    # same trajectory and the same solid domains
+    assert np.abs(parts["X"] - out["X"].detach().numpy()[:, :D]).max() < 1e-7
+    tw = Twin(c["ocfg"])
+    own_ref = tw.owner(out["X"].detach().numpy(), c["R"]).reshape(owner.shape)
+    assert np.array_equal(owner, own_ref)
+    r = res[0]
+    for k in ("X", "U", "W", "theta", "A", "ratio"):
+        _close(r[k], ref[k], what=k)
+    _close(r["alpha"], ref["alpha"], what="alpha")
+    _close(gf[0][1:], ref["field"][1:], what="field")
+
+
+@gpu
+def test_adjoint_checkpointing_and_batching_agree():
+    """Segment lengths 1, 4 and all steps, and a batch of 3 copies, give the
+    same gradients (the recomputation replays the recorded forward bit for bit)."""
+    D, n, per, pos, R, ratio, K, tau, alpha, g = CASES["2d"]
+    c = _case(D, n, per, pos, R, ratio, K, tau, alpha, g, seed=5)
+    steps = 10
+    seeds, sfield = _seeds(c, seed=9)
+    runs = [_gpu_adjoint(c, steps, L, seeds, sfield) for L in (0, 1, 4, steps)]
+    runs.append(_gpu_adjoint(c, steps, 4, seeds, sfield, ninst=3))
+    base = runs[0][0][0]
+    for res, gf, _, _ in runs[1:]:
+        for r in res:
+            for k in ("X", "U", "W", "theta", "A", "ratio"):
+                _close(r[k], base[k], rel=1e-10, what=k)
+            _close(r["alpha"], base["alpha"], rel=1e-10, what="alpha")
+        for f in gf:
+            _close(f, runs[0][1][0], rel=1e-6, what="field")
+
+
+@gpu
+def test_adjoint_of_sedimenting_disk_matches_oracle_finite_differences():
+    """J = final height of a disk settling in a closed box (the adjoint
+    workload's physics at a reduced size): dJ/d(ratio, alpha, X0) from the GPU
+    adjoint against (J(+h) - J(-h)) / 2h of the FP64 oracle, h = 1e-4, on a
+    window in which the solid domains do not change between the two runs."""
+    nx, ny, steps, h = 60, 160, 80, 1e-4
+    pos = np.array([[nx / 2 + 3.3, 0.8 * ny]])
+    R, ratio0, alpha0, g = np.array([6.0]), np.array([1.5]), 0.9, (0, -1e-5, 0)
+    cfg = lbm.make_config(lattice=9, n=(nx, ny, 1), bc=[1, 1, 0], tau=1.0, alpha=alpha0, g_grav=g,
+                          max_particles=1, max_radius=8)
+    sim = lbm.LBM(cfg)
+    sim.add_particles(0, pos, R, ratio0)
+    sim.adjoint_forward(steps, 0)
+    res = sim.adjoint_backward([{"X": np.array([[0.0, 1.0]])}])[0]
+    sim.close()
+
+    def J(alpha=alpha0, ratio=ratio0, X=pos):
+        oc = oracle.make_config(D=2, n=(nx, ny, 1), periodic=(0, 0, 1), tau=1.0, alpha=alpha, g_grav=g)
+        s = oracle.Sim(oc)
+        s.add_particles(X, R, ratio)
+        owners = []
+        for _ in range(steps):
+            owners.append(s.owner_map().copy())
+            s.step(1)
+        return s.particles()["X"][0, 1], owners
+
+    def central(**pm):
+        (Jp, op), (Jm, om) = J(**pm["p"]), J(**pm["m"])
+        assert all(np.array_equal(a, b) for a, b in zip(op, om))
+        return (Jp - Jm) / (2 * h)
+
+    fd_ratio = central(p=dict(ratio=ratio0 + h), m=dict(ratio=ratio0 - h))
+    fd_alpha = central(p=dict(alpha=alpha0 + h), m=dict(alpha=alpha0 - h))
+    xp, xm = pos.copy(), pos.copy()
+    xp[0, 0] += h
+    xm[0, 0] -= h
+    fd_x = central(p=dict(X=xp), m=dict(X=xm))
+    yp, ym = pos.copy(), pos.copy()
+    yp[0, 1] += h
+    ym[0, 1] -= h
+    fd_y = central(p=dict(X=yp), m=dict(X=ym))
+    assert abs(res["ratio"][0] - fd_ratio) <= 1e-4 * abs(fd_ratio), (res["ratio"], fd_ratio)
+    assert abs(res["alpha"] - fd_alpha) <= 1e-4 * abs(fd_alpha) + 1e-9, (res["alpha"], fd_alpha)
+    assert abs(res["X"][0, 0] - fd_x) <= 1e-4 * abs(fd_y) + 1e-9, (res["X"], fd_x)
+    assert abs(res["X"][0, 1] - fd_y) <= 1e-4 * abs(fd_y), (res["X"], fd_y)
+
+
+@gpu
+def test_adjoint_needs_a_recorded_forward():
+    cfg = lbm.make_config(lattice=9, n=(32, 32, 1), max_particles=1)
+    sim = lbm.LBM(cfg)
+    sim.add_particles(0, [[16.0, 16.0]], [4.0], [1.2])
+    with pytest.raises(lbm.LBMError) as ei:
+        sim.adjoint_backward()
+    assert ei.value.status == -6
+    sim.adjoint_forward(4)
+    sim.step(1)  # changes the state: the recording no longer applies
+    with pytest.raises(lbm.LBMError) as ei:
+        sim.adjoint_backward()
+    assert ei.value.status == -6
+    sim.close()
