@@ -199,6 +199,58 @@ def run_reference(args, ws_n, rank):
     }))
 
 
+def adjoint_leg(lbm, torch, rank, nsteps):
+    """Cost of the discrete adjoint on the disk-settling workload (400 x 1600,
+    R = 12, ratio 1.5, J = final height): plain forward, checkpointed forward
+    and backward sweep (segment recomputation included), one instance and a
+    batch of 16 seeds in one context."""
+    from paper_2511_01629_gb300 import workloads as W
+    out = {"workload": "D2Q9 400x1600 closed box, one disk R=12 ratio 1.5 at (200+U(-20,20), 1280), "
+                       "J = final height; gradients w.r.t. ratio, alpha, initial x",
+           "steps": nsteps, "segment": "ceil(sqrt(steps))"}
+
+    def run(batch):
+        ws = [W.adjoint_disk(rank * 100 + s, steps=nsteps) for s in range(batch)]
+        times = {}
+        for rep in range(2):  # the first pass allocates and captures graphs
+            sim = lbm.from_workloads(ws)
+            sim.set_graphs(16)
+            st = sim.stream
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize()
+            ev[0].record(st)
+            sim.step(nsteps)
+            ev[1].record(st)
+            sim.close()
+            sim = lbm.from_workloads(ws)
+            sim.set_graphs(16)
+            torch.cuda.synchronize()
+            ev[2].record(st)
+            sim.adjoint_forward(nsteps, 0)
+            ev[3].record(st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grads = sim.adjoint_backward([{"X": np.array([[0.0, 1.0]])}] * batch)
+            torch.cuda.synchronize()
+            tb = (time.perf_counter() - t0) * 1e3
+            sim.close()
+            times = {"forward_ms": ev[0].elapsed_time(ev[1]), "checkpointed_forward_ms": ev[2].elapsed_time(ev[3]),
+                     "backward_ms": tb}
+        times["ratio"] = times["backward_ms"] / times["forward_ms"]
+        times["ratio_total"] = (times["checkpointed_forward_ms"] + times["backward_ms"]) / times["forward_ms"]
+        times["grad_instance0"] = {"dY/dratio": float(grads[0]["ratio"][0]), "dY/dalpha": grads[0]["alpha"],
+                                   "dY/dX0": float(grads[0]["X"][0, 0])}
+        return times
+
+    import numpy as np
+    one = run(1)
+    out.update(one)
+    out["batch16"] = run(16)
+    out["note"] = ("ratio = backward sweep (recompute + adjoint kernels) / plain forward of the same "
+                   "steps; ratio_total adds the checkpointed forward")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,6 +264,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fp16-leg", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=5000)
     ap.add_argument("--shape", default=None,
                     help="fluid kernel shape vec,rows,warps (vec 0 = TMA pipeline) instead of autotuning")
     ap.add_argument("--kernel-only", action="store_true",
@@ -358,7 +412,12 @@ def main():
                                              "kernel_ms": r16["kernel_ms"],
                                              "traffic": traffic_per_launch("fp16", args.workload)},
                                 "speedup_vs_fp32": v16 / value}
-    line["adjoint_forward_ratio"] = None
+    if not args.no_adjoint and args.workload == "many_disks":
+        adj = adjoint_leg(lbm, torch, rank, args.adjoint_steps)
+        line["adjoint_forward_ratio"] = adj["ratio"]
+        line["adjoint"] = adj
+    else:
+        line["adjoint_forward_ratio"] = None
     if rank == 0 and not args.no_cpu_baseline:
         ws_c = make_workloads(args.workload, 0)
         steps_c = 3 if ws_c[0].nodes > 1e6 else 20

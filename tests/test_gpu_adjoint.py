@@ -227,3 +227,36 @@ def test_adjoint_needs_a_recorded_forward():
         sim.adjoint_backward()
     assert ei.value.status == -6
     sim.close()
+
+
+@gpu
+def test_autograd_function_matches_twin():
+    """torch.autograd through ParticleTrajectory (two instances, particles in
+    contact, K = 2) against autograd of the FP64 twin, instance by instance."""
+    from paper_2511_01629_gb300.autograd import sedimentation_factory, trajectory
+    n, R, g, steps = (40, 48, 1), np.array([4.0, 3.5]), (0, -1e-4, 0), 15
+    fac = sedimentation_factory(n, R, tau=1.0, g_grav=g, K=2)
+    alpha = torch.tensor([0.9, 0.8], dtype=F64, requires_grad=True)
+    ratio = torch.tensor([[1.5, 1.7], [1.3, 1.9]], dtype=F64, requires_grad=True)
+    X0 = torch.tensor([[[15.2, 30.1], [22.5, 27.5]], [[14.7, 29.0], [21.7, 26.2]]], dtype=F64, requires_grad=True)
+    U0 = torch.tensor([[[1e-4, 0.0], [0.0, -2e-4]], [[0.0, 1e-4], [3e-4, 0.0]]], dtype=F64, requires_grad=True)
+    X, U = trajectory(alpha, ratio, X0, U0, fac, steps, 4)
+    (X[..., 1].sum() + 10.0 * U[..., 0].sum()).backward()
+    for b in range(2):
+        ocfg = oracle.make_config(D=2, n=n, periodic=(0, 0, 1), tau=1.0, alpha=float(alpha[b].detach()), g_grav=g, K=2)
+        a = torch.tensor(float(alpha[b]), dtype=F64, requires_grad=True)
+        r = ratio[b].detach().clone().requires_grad_(True)
+        x = torch.zeros(2, 3, dtype=F64)
+        x[:, :2] = X0[b].detach()
+        x.requires_grad_(True)
+        u = torch.zeros(2, 3, dtype=F64)
+        u[:, :2] = U0[b].detach()
+        u.requires_grad_(True)
+        z = torch.zeros(2, 3, dtype=F64)
+        f0 = torch.zeros(9, n[0] * n[1], dtype=F64)
+        out = Twin(ocfg).run(f0, x, u, z, z, z, R, r, a, steps)
+        (out["X"][:, 1].sum() + 10.0 * out["U"][:, 0].sum()).backward()
+        _close(alpha.grad[b].item(), a.grad.item(), what="alpha")
+        _close(ratio.grad[b].numpy(), r.grad.numpy(), what="ratio")
+        _close(X0.grad[b].numpy(), x.grad[:, :2].numpy(), what="X0")
+        _close(U0.grad[b].numpy(), u.grad[:, :2].numpy(), what="U0")
