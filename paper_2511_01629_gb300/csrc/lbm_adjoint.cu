@@ -38,8 +38,8 @@ namespace {
 //   u = m + a/2,  p = (s - kuu u.u) / sum A.
 template <int Q>
 __device__ __forceinline__ void node_adjoint(const float* f, const float* a, const float* lam, bool solid,
-                                             const float* ubp, const CollK& k, float* fb, float* ab,
-                                             float* alb) {
+                                             bool any_solid, const float* ubp, const CollK& k, float* fb,
+                                             float* ab, float* alb) {
     using L = Lat<Q>;
     constexpr int D = L::D;
     constexpr int QS = Q - 1;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void node_adjoint(const float* f, const float* a, con
         Gb[q - 1] = k.fA[cls] * lam[q - 1];
     }
     *alb = 0.f;
-    if (solid) {
+    if (any_solid) {  // warp-uniform: the penalty terms of the solid lanes
         float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Pi_neq: xx yy zz xy xz yz
         float Pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // its adjoint
 #pragma unroll
@@ -80,7 +80,7 @@ __device__ __forceinline__ void node_adjoint(const float* f, const float* a, con
             P[3] += cx * cy * fn;
             P[4] += cx * cz * fn;
             P[5] += cy * cz * fn;
-            const float wq = 1.5f * k.alpha * L::A(q) * lam[q - 1];
+            const float wq = solid ? 1.5f * k.alpha * L::A(q) * lam[q - 1] : 0.f;
             Pb[0] += wq * (cx * cx - (1.0f / 3.0f));
             Pb[1] += wq * (cy * cy - (1.0f / 3.0f));
             Pb[2] += wq * (cz * cz - (1.0f / 3.0f));
@@ -95,7 +95,7 @@ __device__ __forceinline__ void node_adjoint(const float* f, const float* a, con
             const float cx = (float)L::c(q, 0), cy = (float)L::c(q, 1), cz = (float)L::c(q, 2);
             const float pcc = cx * cx * P[0] + cy * cy * P[1] + cz * cz * P[2] +
                               2.0f * (cx * cy * P[3] + cx * cz * P[4] + cy * cz * P[5]);
-            al = fmaf(lam[q - 1] * 1.5f * L::A(q), pcc - trP, al);
+            al = fmaf(solid ? lam[q - 1] * 1.5f * L::A(q) : 0.f, pcc - trP, al);
             const float nu = cx * cx * Pb[0] + cy * cy * Pb[1] + cz * cz * Pb[2] +
                              2.0f * (cx * cy * Pb[3] + cx * cz * Pb[4] + cy * cz * Pb[5]);
             fb[q - 1] += nu;
@@ -143,55 +143,86 @@ __device__ __forceinline__ void node_adjoint(const float* f, const float* a, con
 }
 
 // Pre-collision population q at node (x, y, z) of step n: pull streaming
-// from the recorded populations (bounce-back with the wall term at walls).
-template <int Q, class S>
-__device__ __forceinline__ float pull_pre(const InstDesc& in, const S* __restrict__ fin, int q, int x, int y,
-                                          int z, bool interior) {
+// from the recorded populations, with bounce-back and the wall term where
+// x - c_q lies beyond a wall (the first such axis names the wall, as in the
+// forward kernels).  Selects instead of branches, so that the lanes of a warp
+// on a face stay together.
+template <int Q, class S, int q>
+__device__ __forceinline__ float pull_pre_any(const InstDesc& in, const S* __restrict__ fin, int x, int y, int z,
+                                              int qs) {
     using L = Lat<Q>;
-    if (interior) {
-        const long long off = ((long long)(z - L::c(q, 2)) * in.n[1] + (y - L::c(q, 1))) * in.pitch +
-                              (x - L::c(q, 0));
-        return VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (long long)(q - 1) * in.qstride + off, in.s_load);
+    constexpr int c[3] = {L::c(q, 0), L::c(q, 1), L::c(q, 2)};
+    int src[3] = {x - c[0], y - c[1], z - c[2]};
+    int axis = -1, face = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (c[d] == 0) continue;
+        const bool out = src[d] < 0 || src[d] >= in.n[d];
+        if (out && in.periodic[d]) src[d] += src[d] < 0 ? in.n[d] : -in.n[d];
+        else if (out && axis < 0) {
+            axis = d;
+            face = src[d] < 0 ? 0 : 1;
+        }
     }
-    return pull_scalar<Q, S>(in, fin, q, x, y, z);
+    const int node = (z * in.n[1] + y) * in.pitch + x;
+    const int off = axis >= 0 ? (L::opp(q) - 1) * qs + node
+                              : (q - 1) * qs + (src[2] * in.n[1] + src[1]) * in.pitch + src[0];
+    const float v = VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + off, in.s_load);
+    return axis >= 0 ? v + in.wterm[axis][face][q] : v;
 }
 
 // Transposed streaming: the adjoint of f*_q at x is the adjoint of f_q at
 // x + c_q (wrapped on periodic axes), or of f_opp(q) at x when x + c_q lies
 // beyond a wall (the population bounced back at x).
-template <int Q>
-__device__ __forceinline__ float pull_lam(const InstDesc& in, const float* __restrict__ lam, int q, int x, int y,
-                                          int z, bool interior) {
+template <int Q, int q>
+__device__ __forceinline__ float pull_lam_any(const InstDesc& in, const float* __restrict__ lam, int x, int y, int z,
+                                              int qs) {
     using L = Lat<Q>;
-    if (interior) {
-        const long long off = ((long long)(z + L::c(q, 2)) * in.n[1] + (y + L::c(q, 1))) * in.pitch +
-                              (x + L::c(q, 0));
-        return __ldg(lam + (long long)(q - 1) * in.qstride + off);
-    }
-    int dst[3] = {x + L::c(q, 0), y + L::c(q, 1), z + L::c(q, 2)};
+    constexpr int c[3] = {L::c(q, 0), L::c(q, 1), L::c(q, 2)};
+    int dst[3] = {x + c[0], y + c[1], z + c[2]};
     bool wall = false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        if (dst[d] < 0 || dst[d] >= in.n[d]) {
-            if (in.periodic[d]) dst[d] = dst[d] < 0 ? dst[d] + in.n[d] : dst[d] - in.n[d];
-            else wall = true;
-        }
+        if (c[d] == 0) continue;
+        const bool out = dst[d] < 0 || dst[d] >= in.n[d];
+        if (out && in.periodic[d]) dst[d] += dst[d] < 0 ? in.n[d] : -in.n[d];
+        else if (out) wall = true;
     }
-    if (wall) {
-        const long long off = ((long long)z * in.n[1] + y) * in.pitch + x;
-        return __ldg(lam + (long long)(L::opp(q) - 1) * in.qstride + off);
-    }
-    const long long off = ((long long)dst[2] * in.n[1] + dst[1]) * in.pitch + dst[0];
-    return __ldg(lam + (long long)(q - 1) * in.qstride + off);
+    const int node = (z * in.n[1] + y) * in.pitch + x;
+    const int off = wall ? (L::opp(q) - 1) * qs + node : (q - 1) * qs + (dst[2] * in.n[1] + dst[1]) * in.pitch + dst[0];
+    return __ldg(lam + off);
 }
+
+template <int Q, class S, int q>
+struct PullAll {
+    static __device__ __forceinline__ void pre(const InstDesc& in, const S* fin, int x, int y, int z, int qs,
+                                               float* f) {
+        f[q - 1] = pull_pre_any<Q, S, q>(in, fin, x, y, z, qs);
+        PullAll<Q, S, q + 1>::pre(in, fin, x, y, z, qs, f);
+    }
+    static __device__ __forceinline__ void lam(const InstDesc& in, const float* ls, int x, int y, int z, int qs,
+                                               float* l) {
+        l[q - 1] = pull_lam_any<Q, q>(in, ls, x, y, z, qs);
+        PullAll<Q, S, q + 1>::lam(in, ls, x, y, z, qs, l);
+    }
+};
+template <int Q, class S>
+struct PullAll<Q, S, Q> {
+    static __device__ __forceinline__ void pre(const InstDesc&, const S*, int, int, int, int, float*) {}
+    static __device__ __forceinline__ void lam(const InstDesc&, const float*, int, int, int, int, float*) {}
+};
 
 }  // namespace
 
 // ------------------------------------------------------------ fluid sweep --
 // lam_mode: 0 = pull the adjoint of step n + 1, 1 = read a field seed [Q][N]
 // (the adjoint of the final post-collision populations), 2 = zero.
+// One block per tile of the forward kernel's shape (its candidate lists are
+// per tile); each warp takes whole x-rows of the tile and its lanes stride
+// along x, so the loads of a population are coalesced.  Interior nodes use
+// per-population element offsets precomputed once per block.
 template <int Q, class S>
-__global__ void __launch_bounds__(256) k_adj_fluid(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(256, Q == 9 ? 3 : 2) k_adj_fluid(const InstDesc* __restrict__ insts,
                                                    const AdjFluid* __restrict__ afs,
                                                    const uint16_t* __restrict__ tile_inst, int lam_mode,
                                                    Shape sh) {
@@ -199,6 +230,7 @@ __global__ void __launch_bounds__(256) k_adj_fluid(const InstDesc* __restrict__ 
     constexpr int D = L::D;
     constexpr int QS = Q - 1;
     __shared__ Cand cand[LIST_CAP];
+    __shared__ int offF[QS], offL[QS];  // source offsets of the forward and the transposed pull
     const int t = blockIdx.x;
     const int ii = tile_inst[t];
     const InstDesc& in = insts[ii];
@@ -208,7 +240,16 @@ __global__ void __launch_bounds__(256) k_adj_fluid(const InstDesc* __restrict__ 
     const int ntx = in.ntile[0], nty = in.ntile[1];
     const int tx = local % ntx, rest = local / ntx;
     const int x0 = tx * tw, y0 = (rest % nty) * sh.ty, z0 = (rest / nty) * sh.tz;
-    const int lane = threadIdx.x & 31;
+    const int nx = in.n[0], ny = in.n[1], nz = in.n[2];
+    const int pitch = in.pitch;
+    const int qs = (int)in.qstride;  // (Q - 1) * qstride < 2^31 (validated at creation)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (threadIdx.x < QS) {
+        const int q = threadIdx.x + 1;
+        const int sh_f = (L::c(q, 2) * ny + L::c(q, 1)) * pitch + L::c(q, 0);
+        offF[threadIdx.x] = (q - 1) * qs - sh_f;
+        offL[threadIdx.x] = (q - 1) * qs + sh_f;
+    }
     int ncand = 0;
     if (in.np > 0) {
         ncand = min(af.lcnt[local], LIST_CAP);
@@ -235,40 +276,58 @@ __global__ void __launch_bounds__(256) k_adj_fluid(const InstDesc* __restrict__ 
     geo.prec = af.prec;
     const CollK ck = make_collk<Q>(make_collp(in));
     const S* __restrict__ fin = static_cast<const S*>(af.fin);
-    const long long N = (long long)in.n[0] * in.n[1] * in.n[2];
-    const int tot = tw * sh.ty * sh.tz;
-    for (int i0 = 0; i0 < tot; i0 += blockDim.x) {
-        const int i = i0 + threadIdx.x;
-        const int x = x0 + i % tw, r = i / tw;
+    const float* __restrict__ lsrc = af.lam_src;
+    float* __restrict__ ldst = af.lam_dst;
+    const float sl = in.s_load;
+    const float gd[3] = {in.gdrive[0], in.gdrive[1], in.gdrive[2]};
+    const long long N = (long long)nx * ny * nz;
+    const int w = min(tw, nx - x0);
+    const int wpad = (w + 31) & ~31;
+    const int rows = sh.ty * sh.tz;
+    for (int r = warp; r < rows; r += nwarps) {
         const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
-        const bool valid = i < tot && x < in.n[0] && y < in.n[1] && z < in.n[2];
-        int own = -1;
-        float ab[3] = {0.f, 0.f, 0.f}, alb = 0.f;
-        if (valid) {
-            const bool interior = x >= 1 && x + 1 < in.n[0] && y >= 1 && y + 1 < in.n[1] &&
-                                  (D == 2 || (z >= 1 && z + 1 < in.n[2]));
+        if (y >= ny || z >= nz) continue;  // warp-uniform
+        const bool row_in = y >= 1 && y + 1 < ny && (D == 2 || (z >= 1 && z + 1 < nz));
+        const int rowoff = (z * ny + y) * pitch;
+        for (int xo = lane; xo < wpad; xo += 32) {
+            const int x = x0 + xo;
+            const bool valid = xo < w;
+            const int xs = valid ? x : x0;  // lanes beyond the row compute on a valid node, store nothing
+            const int node = rowoff + xs;
+            // warp-uniform: every lane's stencil stays inside the box
+            const bool interior = __all_sync(0xffffffffu, row_in && xs >= 1 && xs + 1 < nx);
             float f[QS], lam[QS];
+            if (interior) {
 #pragma unroll
-            for (int q = 1; q < Q; ++q) f[q - 1] = pull_pre<Q, S>(in, fin, q, x, y, z, interior);
-            const long long node = ((long long)z * in.n[1] + y) * in.n[0] + x;
+                for (int q = 0; q < QS; ++q)
+                    f[q] = VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (node + offF[q]), sl);
+            } else {
+                PullAll<Q, S, 1>::pre(in, fin, xs, y, z, qs, f);
+            }
             if (lam_mode == 0) {
+                if (interior) {
 #pragma unroll
-                for (int q = 1; q < Q; ++q) lam[q - 1] = pull_lam<Q>(in, af.lam_src, q, x, y, z, interior);
+                    for (int q = 0; q < QS; ++q) lam[q] = __ldg(lsrc + (node + offL[q]));
+                } else {
+                    PullAll<Q, S, 1>::lam(in, lsrc, xs, y, z, qs, lam);
+                }
             } else if (lam_mode == 1) {
+                const long long nd = ((long long)z * ny + y) * nx + xs;
 #pragma unroll
-                for (int q = 1; q < Q; ++q) lam[q - 1] = __ldg(af.lam_src + (long long)q * N + node);
+                for (int q = 1; q < Q; ++q) lam[q - 1] = __ldg(lsrc + (long long)q * N + nd);
             } else {
 #pragma unroll
                 for (int q = 0; q < QS; ++q) lam[q] = 0.f;
             }
-            float a[3] = {in.gdrive[0], in.gdrive[1], in.gdrive[2]};
+            float a[3] = {gd[0], gd[1], gd[2]};
             float ubp[3] = {0.f, 0.f, 0.f};
+            int own = -1;
             if (ncand > 0) {
-                const int xyz[3] = {x, y, z};
-                int sl = -1;
-                own = owner_of<D>(geo, cand, ncand, xyz, &sl);
+                const int xyz[3] = {xs, y, z};
+                int slt = -1;
+                own = owner_of<D>(geo, cand, ncand, xyz, &slt);
                 if (own >= 0) {
-                    const Cand& cd = cand[sl];
+                    const Cand& cd = cand[slt];
                     float rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                     for (int d = 0; d < D; ++d)
@@ -281,30 +340,33 @@ __global__ void __launch_bounds__(256) k_adj_fluid(const InstDesc* __restrict__ 
                     ubp[1] = cf[1] + (cf[5] * rr[0] - cf[3] * rr[2]);
                     ubp[2] = D == 3 ? cf[2] + (cf[3] * rr[1] - cf[4] * rr[0]) : 0.f;
                 }
+                if (!valid) own = -1;
             }
-            float fb[QS];
-            node_adjoint<Q>(f, a, lam, own >= 0, ubp, ck, fb, ab, &alb);
-            const long long off = ((long long)z * in.n[1] + y) * in.pitch + x;
+            float fb[QS], ab[3], alb;
+            const bool any_solid = __any_sync(0xffffffffu, own >= 0);
+            node_adjoint<Q>(f, a, lam, own >= 0, any_solid, ubp, ck, fb, ab, &alb);
+            if (valid) {
 #pragma unroll
-            for (int q = 1; q < Q; ++q) af.lam_dst[(long long)(q - 1) * in.qstride + off] = fb[q - 1];
-        }
-        // per-particle sums of the adjoint acceleration and alpha derivative
-        unsigned pend = __ballot_sync(0xffffffffu, own >= 0);
-        while (pend) {
-            const int leader = __ffs(pend) - 1;
-            const int p = __shfl_sync(0xffffffffu, own, leader);
-            const bool mine = own == p;
-            float v[4] = {mine ? ab[0] : 0.f, mine ? ab[1] : 0.f, mine ? ab[2] : 0.f, mine ? alb : 0.f};
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            if (lane == leader) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < D || k == 3) atomicAdd(af.Abar + 4LL * p + k, (double)v[k]);
+                for (int q = 0; q < QS; ++q) ldst[node + q * qs] = fb[q];
             }
-            pend &= ~__ballot_sync(0xffffffffu, mine);
+            // per-particle sums of the adjoint acceleration and alpha derivative
+            unsigned pend = __ballot_sync(0xffffffffu, own >= 0);
+            while (pend) {
+                const int leader = __ffs(pend) - 1;
+                const int p = __shfl_sync(0xffffffffu, own, leader);
+                const bool mine = own == p;
+                float v[4] = {mine ? ab[0] : 0.f, mine ? ab[1] : 0.f, mine ? ab[2] : 0.f, mine ? alb : 0.f};
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+                if (lane == leader) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < D || k == 3) atomicAdd(af.Abar + 4LL * p + k, (double)v[k]);
+                }
+                pend &= ~__ballot_sync(0xffffffffu, mine);
+            }
         }
     }
 }
@@ -320,9 +382,11 @@ __global__ void k_adj_pull_out(const InstDesc* __restrict__ insts, int inst, con
     if (i >= N) return;
     const int x = (int)(i % in.n[0]), y = (int)((i / in.n[0]) % in.n[1]),
               z = (int)(i / ((long long)in.n[0] * in.n[1]));
+    float v[Q - 1];
+    PullAll<Q, float, 1>::lam(in, lam, x, y, z, (int)in.qstride, v);
     out[i] = 0.f;
 #pragma unroll
-    for (int q = 1; q < Q; ++q) out[(long long)q * N + i] = pull_lam<Q>(in, lam, q, x, y, z, false);
+    for (int q = 1; q < Q; ++q) out[(long long)q * N + i] = v[q - 1];
 }
 
 // --------------------------------------------------------- particle sweep --
@@ -332,7 +396,7 @@ namespace {
 // with the lattice's minimum image, and mirror images across wall planes.
 __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, double* G) {
     G[0] = G[1] = G[2] = 0.0;
-    const double idl = 1.0 / in.delta;
+    const double idl = in.pconst[PCONST_N * i + PC_INVDELTA];
     for (int j = 0; j < in.np; ++j) {
         if (j == i) continue;
         double dv[3] = {0, 0, 0};
@@ -349,7 +413,7 @@ __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, do
         const double d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
         if (d2 > range * range) continue;
         const double s = (range - sqrt(d2)) * idl;
-        for (int d = 0; d < 3; ++d) G[d] += dv[d] * s * s / in.eps_p;
+        for (int d = 0; d < 3; ++d) G[d] += dv[d] * s * s * in.inv_eps_p;
     }
     for (int d = 0; d < D; ++d) {
         if (in.periodic[d]) continue;
@@ -359,7 +423,7 @@ __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, do
             const double range = 2.0 * in.R[i] + in.delta;
             if (fabs(diff) <= range) {
                 const double s = (range - fabs(diff)) * idl;
-                G[d] += diff * s * s / in.eps_w;
+                G[d] += diff * s * s * in.inv_eps_w;
             }
         }
     }
@@ -371,9 +435,8 @@ __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, do
 // phi'(d) = s^2 1 - (2 s / (delta |d|)) d d^T (even in d):
 //   Yb_m = sum_j phi'(d_mj) (k_m v_m - k_j v_j) + walls 2 kw_m psi'(diff) v_m.
 __device__ void force_jt(const InstDesc& in, int D, const double* Y, const double* v, int m, double* out) {
-    const double idl = 1.0 / in.delta;
-    const double gC = in.rho_f * in.gmag;
-    const double km = (in.ratio[m] - 1.0) * gC / in.eps_p;
+    const double idl = in.pconst[PCONST_N * m + PC_INVDELTA];
+    const double km = in.pconst[PCONST_N * m + PC_CPAIR];  // C_m / eps_p
     double acc[3] = {0, 0, 0};
     for (int j = 0; j < in.np; ++j) {
         if (j == m) continue;
@@ -392,14 +455,14 @@ __device__ void force_jt(const InstDesc& in, int D, const double* Y, const doubl
         if (d2 > range * range || d2 == 0.0) continue;
         const double dist = sqrt(d2);
         const double s = (range - dist) * idl;
-        const double kj = (in.ratio[j] - 1.0) * gC / in.eps_p;
+        const double kj = in.pconst[PCONST_N * j + PC_CPAIR];
         double w[3];
         for (int d = 0; d < 3; ++d) w[d] = km * v[3 * m + d] - kj * v[3 * j + d];
         const double dw = dv[0] * w[0] + dv[1] * w[1] + dv[2] * w[2];
-        const double g = 2.0 * s * idl / dist;
+        const double g = 2.0 * s * idl * rcp64(dist);
         for (int d = 0; d < 3; ++d) acc[d] += s * s * w[d] - g * dv[d] * dw;
     }
-    const double kw = (in.ratio[m] - 1.0) * gC / in.eps_w;
+    const double kw = in.pconst[PCONST_N * m + PC_CWALL];  // C_m / eps_w
     for (int d = 0; d < D; ++d) {
         if (in.periodic[d]) continue;
         const double walls[2] = {-0.5, in.n[d] - 0.5};
@@ -436,7 +499,6 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
     //    the density ratios (a = (1 - 1/ratio) g + A on solid nodes) and of alpha
     double al = 0.0;
     for (int p = tid; p < np; p += nt) {
-        const double ratio = in.ratio[p];
         double Ap[3], gsum = 0.0;
         for (int d = 0; d < 3; ++d) {
             const double fl = b.Abar[4 * p + d];
@@ -447,7 +509,8 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
         }
         al += b.Abar[4 * p + 3];
         b.Abar[4 * p + 3] = 0.0;
-        b.rb[p] += gsum / (ratio * ratio);
+        const double iratio = in.pconst[PCONST_N * p + PC_INVRHOS] * in.rho_f;
+        b.rb[p] += gsum * iratio * iratio;
         // state after step n: X' = Xk_K (wrapped), U' = U^n, W' = W^n,
         // theta' = theta + (W^n + W)/2, A' = 2 (Xk_K - X - Ubar)
         for (int d = 0; d < 3; ++d) {
@@ -475,10 +538,8 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
             double G1[3], G2[3];
             unit_force(in, D, Xp, p, G1);
             unit_force(in, D, Xs, p, G2);
-            const double ratio = in.ratio[p];
-            const double Cp = (ratio - 1.0) * gC;
-            const double cnt = sp.st1[16 * p + 15];
-            const double c = 0.25 * h * h / (ratio * in.rho_f * cnt);
+            const double Cp = (in.ratio[p] - 1.0) * gC;
+            const double c = 0.25 * h * h * in.pconst[PCONST_N * p + PC_INVRHOS] * rcp64(sp.st1[16 * p + 15]);
             for (int d = 0; d < 3; ++d) {
                 b.F1[(j - 1) * s3 + 3 * p + d] = G1[d];
                 b.F2[(j - 1) * s3 + 3 * p + d] = G2[d];
@@ -490,17 +551,17 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
     // 3. reverse sub-steps: Xk_j = Xs_j + c (F1(Xk_{j-1}) + F2(Xs_j)), Xs_j = Xk_{j-1} + h Ubar
     for (int j = K; j >= 1; --j) {
         for (int p = tid; p < np; p += nt) {
-            const double ratio = in.ratio[p];
-            const double Cp = (ratio - 1.0) * gC;
-            const double cnt = sp.st1[16 * p + 15];
-            const double c = 0.25 * h * h / (ratio * in.rho_f * cnt);
+            const double Cp = (in.ratio[p] - 1.0) * gC;
+            const double irs = in.pconst[PCONST_N * p + PC_INVRHOS];  // 1 / (rho_s)
+            const double c = 0.25 * h * h * irs * rcp64(sp.st1[16 * p + 15]);
+            const double iratio = irs * in.rho_f;
             double rbp = 0.0;
             for (int d = 0; d < 3; ++d) {
                 const double xkb = b.Xkb[3 * p + d];
                 const double Gs = b.F1[(j - 1) * s3 + 3 * p + d] + b.F2[(j - 1) * s3 + 3 * p + d];
                 b.v[3 * p + d] = c * xkb;
                 // d c / d ratio = -c / ratio, d C / d ratio = rho_f |g|
-                rbp += xkb * (-c / ratio * Cp * Gs + c * gC * Gs);
+                rbp += xkb * (-c * iratio * Cp * Gs + c * gC * Gs);
             }
             b.rb[p] += rbp;
         }
@@ -525,7 +586,7 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
     // 4. Ubar = (U^n + U^{n-1})/2, the projection (Eq. 22) and the outputs
     for (int p = tid; p < np; p += nt) {
         const double* g = sp.geo + (long long)NPV * p;
-        const double cnt = g[0];
+        const double icnt = rcp64(g[0]);
         double Unb[3], Wnb[3], Xb[3], W[3], Su[3], Sr[3];
         for (int d = 0; d < 3; ++d) {
             Xb[d] = b.Xb[3 * p + d] + b.Xkb[3 * p + d];
@@ -538,7 +599,7 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
         }
         double mu[3] = {0, 0, 0};
         if (D == 2) {
-            mu[2] = Wnb[2] / (g[4] + g[5]);
+            mu[2] = Wnb[2] * rcp64(g[4] + g[5]);
         } else {
             // I = tr(rr) 1 - rr (symmetric); mu = I^-1 Wnb by cofactors
             const double tr = g[4] + g[5] + g[6];
@@ -546,7 +607,7 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
             const double I01 = -g[7], I02 = -g[8], I12 = -g[9];
             const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
             const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
-            const double idet = 1.0 / (I00 * c00 + I01 * c01 + I02 * c02);
+            const double idet = rcp64(I00 * c00 + I01 * c01 + I02 * c02);
             mu[0] = (c00 * Wnb[0] + c01 * Wnb[1] + c02 * Wnb[2]) * idet;
             mu[1] = (c01 * Wnb[0] + c11 * Wnb[1] + c12 * Wnb[2]) * idet;
             mu[2] = (c02 * Wnb[0] + c12 * Wnb[1] + c22 * Wnb[2]) * idet;
@@ -560,7 +621,7 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
         for (int d = 0; d < D; ++d) Xb[d] += cx[d] + 2.0 * muW * Sr[d] - mu[d] * SrW - W[d] * muSr;
         for (int d = 0; d < 3; ++d) {
             b.Xb[3 * p + d] = d < D ? Xb[d] : 0.0;
-            b.coef[8 * p + d] = (float)(Unb[d] / cnt);
+            b.coef[8 * p + d] = (float)(Unb[d] * icnt);
             b.coef[8 * p + 3 + d] = (float)mu[d];
         }
     }
@@ -576,7 +637,7 @@ __global__ void k_adj_finish(const InstDesc* __restrict__ insts, const AdjBufs* 
     double* o = out + out_off[ii];
     double al = 0.0;
     for (int p = threadIdx.x; p < in.np; p += blockDim.x) {
-        const double ratio = in.ratio[p];
+        const double iratio = in.pconst[PCONST_N * p + PC_INVRHOS] * in.rho_f;
         double gsum = 0.0;
         double* r = o + 1 + 16LL * p;
         for (int d = 0; d < 3; ++d) {
@@ -589,7 +650,7 @@ __global__ void k_adj_finish(const InstDesc* __restrict__ insts, const AdjBufs* 
             r[13 + d] = b.Ab[3 * p + d] + fl;
         }
         al += b.Abar[4 * p + 3];
-        r[0] = b.rb[p] + gsum / (ratio * ratio);
+        r[0] = b.rb[p] + gsum * iratio * iratio;
     }
     __shared__ double red[128];
     red[threadIdx.x] = al;

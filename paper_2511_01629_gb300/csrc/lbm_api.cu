@@ -89,6 +89,7 @@ struct AdjCtx {
     int nsteps = 0, L = 0, nseg = 0;
     std::vector<AdjInst> ai;
     DevBuf d_rdesc, d_rtmaps, d_afl, d_apt, d_abufs, d_out, d_out_off;
+    cudaGraphExec_t seg_exec = nullptr;  // recompute + backward of one full segment
 };
 
 }  // namespace
@@ -287,6 +288,8 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.delta = c.delta;
     d.eps_p = c.eps_p;
     d.eps_w = c.eps_w;
+    d.inv_eps_p = 1.0 / c.eps_p;
+    d.inv_eps_w = 1.0 / c.eps_w;
     d.K = c.K;
     d.hK = 1.0 / c.K;
     d.status = P<int>(ctx->d_status);
@@ -537,8 +540,14 @@ int read_status(lbm_ctx* ctx) {
     return set_err(ctx, LBM_ERR_CAPACITY, "a tile overlaps more particles than its list holds%s");
 }
 
+void adj_drop_graph(AdjCtx& A) {
+    if (A.seg_exec) cudaGraphExecDestroy(A.seg_exec);
+    A.seg_exec = nullptr;
+}
+
 void adj_release(lbm_ctx* ctx) {
     AdjCtx& A = ctx->adj;
+    adj_drop_graph(A);
     for (auto& a : A.ai) {
         for (auto& b : a.ckpt) dfree(ctx, b);
         for (auto& b : a.slot) dfree(ctx, b);
@@ -1171,7 +1180,12 @@ int lbm_adjoint_forward(lbm_ctx* ctx, int nsteps, int seg_len) {
     if (seg_len < 0) return set_err(ctx, LBM_ERR_INVALID, "negative segment length%s");
     AdjCtx& A = ctx->adj;
     A.ready = false;
-    const int L = seg_len > 0 ? std::min(seg_len, nsteps) : std::max(1, (int)ceil(sqrt((double)nsteps)));
+    // an even segment length keeps the parity of the global step equal to that
+    // of the step within its segment, so one set of per-step descriptors (and
+    // one captured graph) serves every segment
+    int L = seg_len > 0 ? seg_len : std::max(1, (int)ceil(sqrt((double)nsteps)));
+    if (L >= nsteps) L = nsteps;
+    else if (L & 1) L += 1;
     const int nseg = (nsteps + L - 1) / L;
     const size_t ssz = ctx->fp16 ? 2 : 4;
     const int ni = (int)ctx->inst.size();
@@ -1326,9 +1340,11 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
         CK(cudaMemcpyAsync(A.d_rtmaps.ptr, tm.data(), sizeof(CUtensorMap) * tm.size(), cudaMemcpyHostToDevice,
                            ctx->st));
     }
-    // per-step views of the backward sweep, for every global step
-    std::vector<AdjFluid> afl((size_t)N * ni);
-    std::vector<AdjPart> apt((size_t)N * ni);
+    // per-step views of the backward sweep, step k of a segment (entry L: the
+    // last step of the whole run when it reads a field seed)
+    const int len_last = N - (nseg - 1) * L;
+    std::vector<AdjFluid> afl((size_t)(L + 1) * ni);
+    std::vector<AdjPart> apt((size_t)L * ni);
     std::vector<AdjBufs> ab(ni);
     std::vector<long long> out_off(ni);
     long long nout = 0;
@@ -1342,27 +1358,28 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
         field_off[i] = foff;
         foff += (long long)ctx->Q * I.n[0] * I.n[1] * I.n[2];
     }
-    for (int n = 0; n < N; ++n) {
-        const int k = n % L;
+    for (int k = 0; k <= L; ++k) {
+        const int kk = k == L ? len_last - 1 : k;
         for (int i = 0; i < ni; ++i) {
             Instance& I = ctx->inst[i];
             AdjInst& a = A.ai[i];
             const size_t n1 = (size_t)std::max(I.np, 1);
             AdjFluid f;
-            f.fin = a.slot[k].ptr;
-            f.prec = P<PRec>(a.rprec) + n1 * k;
-            f.lcnt = P<int>(a.rlcnt) + (size_t)I.ntiles * k;
-            f.lent = P<uint32_t>(a.rlent) + (size_t)I.ntiles * LIST_CAP * k;
-            f.lam_src = (n == N - 1) ? (seed_field ? seed_field + field_off[i] : nullptr) : P<float>(a.fbar[(n + 1) & 1]);
-            f.lam_dst = P<float>(a.fbar[n & 1]);
+            f.fin = a.slot[kk].ptr;
+            f.prec = P<PRec>(a.rprec) + n1 * kk;
+            f.lcnt = P<int>(a.rlcnt) + (size_t)I.ntiles * kk;
+            f.lent = P<uint32_t>(a.rlent) + (size_t)I.ntiles * LIST_CAP * kk;
+            f.lam_src = k == L ? (seed_field ? seed_field + field_off[i] : nullptr) : P<float>(a.fbar[(kk + 1) & 1]);
+            f.lam_dst = P<float>(a.fbar[kk & 1]);
             f.coef = ab[i].coef;
             f.Abar = ab[i].Abar;
-            afl[(size_t)n * ni + i] = f;
+            afl[(size_t)k * ni + i] = f;
+            if (k == L) continue;
             AdjPart pp;
             pp.st0 = P<double>(a.rstate) + 16 * n1 * k;
             pp.st1 = P<double>(a.rstate) + 16 * n1 * (k + 1);
             pp.geo = P<double>(a.rgeo) + NPV * n1 * k;
-            apt[(size_t)n * ni + i] = pp;
+            apt[(size_t)k * ni + i] = pp;
         }
     }
     if ((rc = dalloc(ctx, A.d_afl, sizeof(AdjFluid) * afl.size())) ||
@@ -1393,6 +1410,35 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
     const InstDesc* dI = P<InstDesc>(ctx->d_insts);
     const InstDesc* dR = P<InstDesc>(A.d_rdesc);
     const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
+    // recomputation of a segment of len steps into the slots and records, then
+    // the backward sweep through it (k = len - 1 .. 0); last: the segment holds
+    // the final step of the run, whose adjoint comes from the seed
+    auto enqueue_segment = [&](cudaStream_t st, int len, bool last) -> int {
+        for (int k = 0; k < len; ++k) {
+            const int par = k & 1;
+            const InstDesc* dk = dR + (size_t)k * ni;
+            if (sh.tma)
+                CK(launch_fluid_tma(ctx->Q, ctx->fp16, dk, P<CUtensorMap>(A.d_rtmaps) + (size_t)k * ni * 2,
+                                    P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1, ctx->grid,
+                                    P<int>(ctx->d_tile_ctr), sh.stages, st));
+            else
+                CK(launch_fluid(ctx->Q, ctx->fp16, dk, P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1,
+                                sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), st));
+            if (ctx->np_total > 0)
+                CK(launch_particles(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, K, par ^ 1, sh,
+                                    P<GridBar>(ctx->d_gridbar), fused, st));
+        }
+        for (int k = len - 1; k >= 0; --k) {
+            CK(launch_adj_particles(ctx->D, dI, P<AdjPart>(A.d_apt) + (size_t)k * ni, P<AdjBufs>(A.d_abufs), ni,
+                                    st));
+            const bool final_step = last && k == len - 1;
+            const int mode = final_step ? (seed_field ? 1 : 2) : 0;
+            CK(launch_adj_fluid(ctx->Q, ctx->fp16, dI, P<AdjFluid>(A.d_afl) + (size_t)(final_step ? L : k) * ni,
+                                P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, mode, sh, st));
+        }
+        return LBM_OK;
+    };
+    adj_drop_graph(A);  // descriptors and buffers may have moved since the last capture
     for (int s = nseg - 1; s >= 0; --s) {
         const int len = std::min(L, N - s * L);
         // restore the segment's first state into slot 0, record 0 and the context
@@ -1409,30 +1455,24 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
         }
         if (ctx->np_total > 0)
             CK(launch_publish(dR + (size_t)L * ni, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, 0, sh, ctx->st));
-        // recompute the segment into the slots and records
-        for (int k = 0; k < len; ++k) {
-            const int par = k & 1;
-            const InstDesc* dk = dR + (size_t)k * ni;
-            if (sh.tma)
-                CK(launch_fluid_tma(ctx->Q, ctx->fp16, dk, P<CUtensorMap>(A.d_rtmaps) + (size_t)k * ni * 2,
-                                    P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1, ctx->grid,
-                                    P<int>(ctx->d_tile_ctr), sh.stages, ctx->st));
-            else
-                CK(launch_fluid(ctx->Q, ctx->fp16, dk, P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1,
-                                sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), ctx->st));
-            if (ctx->np_total > 0)
-                CK(launch_particles(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, K, par ^ 1, sh,
-                                    P<GridBar>(ctx->d_gridbar), fused, ctx->st));
+        if (s == nseg - 1) {
+            if ((rc = enqueue_segment(ctx->st, len, true))) return rc;
+            continue;
         }
-        // backward through the segment
-        for (int k = len - 1; k >= 0; --k) {
-            const int n = s * L + k;
-            CK(launch_adj_particles(ctx->D, dI, P<AdjPart>(A.d_apt) + (size_t)n * ni, P<AdjBufs>(A.d_abufs), ni,
-                                    ctx->st));
-            const int mode = n == N - 1 ? (seed_field ? 1 : 2) : 0;
-            CK(launch_adj_fluid(ctx->Q, ctx->fp16, dI, P<AdjFluid>(A.d_afl) + (size_t)n * ni,
-                                P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, mode, sh, ctx->st));
+        // every other segment is a full one: replay one captured graph
+        if (!A.seg_exec) {
+            cudaGraph_t g = nullptr;
+            if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+            const int err = enqueue_segment(ctx->cap, L, false);
+            cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+            if (err) return err;
+            if (e != cudaSuccess) return cuda_err(ctx, e, "adjoint graph capture");
+            e = cudaGraphInstantiate(&A.seg_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "adjoint graph instantiate");
         }
+        CK(cudaGraphLaunch(A.seg_exec, ctx->st));
     }
     CK(launch_adj_finish(dI, P<AdjBufs>(A.d_abufs), P<long long>(A.d_out_off), P<double>(A.d_out), ni, ctx->st));
     if (grad_field)

@@ -166,6 +166,7 @@ struct InstDesc {
     double rho_f;
     double gmag;              // |g_grav|
     double delta, eps_p, eps_w;
+    double inv_eps_p, inv_eps_w;
     double hK;                // 1 / K
     int K;
     int* status;
