@@ -77,6 +77,17 @@ template <int V> struct VecIO<__half, V> {
 };
 
 __device__ __forceinline__ float to_float_scaled(float v, float) { return v; }
+// Two adjacent populations from shared memory (8-byte / 4-byte aligned pair).
+__device__ __forceinline__ float2 smem_pair(const float* p, float) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 smem_pair(const __half* p, float s) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    return make_float2(v.x * s, v.y * s);
+}
+// Two adjacent populations to global memory (aligned pair).
+__device__ __forceinline__ void store_pair(float* p, float2 v, float) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ void store_pair(__half* p, float2 v, float s) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.x * s, v.y * s);
+}
 __device__ __forceinline__ float to_float_scaled(__half v, float s) { return __half2float(v) * s; }
 
 template <class S> __device__ __forceinline__ S to_store(float v, float s);
@@ -185,12 +196,12 @@ __device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int nca
     return best;
 }
 
-// Candidates whose solid domain can reach the 32-node row segment starting
-// at x0 of row (y, z): a uniform test per candidate instead of a test per
+// Candidates whose solid domain can reach the row segment of width nodes
+// starting at x0 of row (y, z): a uniform test per candidate instead of a test per
 // node.  Bit c set = candidate c may own a node of the segment (ncand <= 32).
 template <int D>
 __device__ __forceinline__ unsigned segment_candidates(const Geo& g, const Cand* cand, int ncand, int x0,
-                                                       int y, int z) {
+                                                       int y, int z, int width = 32) {
     unsigned act = 0;
     for (int c = 0; c < ncand; ++c) {
         const Cand& cd = cand[c];
@@ -202,9 +213,9 @@ __device__ __forceinline__ unsigned segment_candidates(const Geo& g, const Cand*
         }
         if (rest < 0.f) continue;
         const float hw = sqrtf(rest) + 1.0f;
-        // nearest distance along x from the centre to the segment [x0, x0 + 31]
+        // nearest distance along x from the centre to the segment [x0, x0 + width - 1]
         const float dx0 = (float)wrap_int(x0 - cd.ref[0], g.n[0], g.per[0]) - cd.frac[0];
-        if (dx0 > hw || dx0 + 31.0f < -hw) {
+        if (dx0 > hw || dx0 + (float)(width - 1) < -hw) {
             if (!g.per[0]) continue;
         }
         act |= 1u << c;
@@ -253,12 +264,20 @@ __device__ __forceinline__ int owner_masked(const Geo& in, const Cand* cand, uns
 //   p = (sum_{q>=1} f_q - (1.5 - 0.5 sum A) u.u) / sum A,
 // the inverse of feq for these coefficients.  Opposite velocities share c.u,
 // c.a and p - u.u/2 + 1.5 (c.u)^2, so the work goes pair by pair.
+//
+// Two nodes at a time: every operation is one packed FP32x2 instruction
+// (FFMA2 / FMUL2 / FADD2, each half rounded like its scalar counterpart), so
+// a lane collides two nodes for the instruction count of one.  Every product,
+// sum and fused multiply-add is written out, so the rounding does not depend
+// on the compiler's contraction choices, and the one-node entry point below
+// (both halves the same node) gives the same bits as the two-node one.
 struct CollK {
     float keep;       // 1 - 1/tau
     float omk;        // 1/tau
     float A[2];       // A for the two weight classes (axis, diagonal/edge)
     float fA[2];      // (1 - 1/2tau) A
     float alpha;
+    float sA[2];      // 1.5 alpha A (penalty)
 };
 template <int Q>
 __device__ __forceinline__ CollK make_collk(const CollP& in) {
@@ -273,26 +292,34 @@ __device__ __forceinline__ CollK make_collk(const CollP& in) {
         // rounded product of the two can bias the momentum of feq
         k.A[i] = A[i];
         k.fA[i] = in.fpref * A[i];
+        k.sA[i] = (1.5f * in.alpha) * A[i];
     }
     k.alpha = in.alpha;
     return k;
 }
 
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b: b * (-1) is exact, so the fused form rounds once, like FADD
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // c_q . v for a compile-time velocity q, without adding zeros
 template <int Q, int q>
-__device__ __forceinline__ float cdot(const float* v) {
+__device__ __forceinline__ float2 cdot2(const float2* v) {
     using L = Lat<Q>;
     constexpr int c0 = L::c(q, 0), c1 = L::c(q, 1), c2 = L::c(q, 2);
-    float r;
+    float2 r;
     if constexpr (c0 != 0) {
-        r = c0 > 0 ? v[0] : -v[0];
-        if constexpr (c1 != 0) r = c1 > 0 ? r + v[1] : r - v[1];
-        if constexpr (c2 != 0) r = c2 > 0 ? r + v[2] : r - v[2];
+        r = c0 > 0 ? v[0] : mul2(v[0], bc2(-1.0f));
+        if constexpr (c1 != 0) r = c1 > 0 ? add2(r, v[1]) : sub2(r, v[1]);
+        if constexpr (c2 != 0) r = c2 > 0 ? add2(r, v[2]) : sub2(r, v[2]);
     } else if constexpr (c1 != 0) {
-        r = c1 > 0 ? v[1] : -v[1];
-        if constexpr (c2 != 0) r = c2 > 0 ? r + v[2] : r - v[2];
+        r = c1 > 0 ? v[1] : mul2(v[1], bc2(-1.0f));
+        if constexpr (c2 != 0) r = c2 > 0 ? add2(r, v[2]) : sub2(r, v[2]);
     } else {
-        r = c2 > 0 ? v[2] : -v[2];
+        r = c2 > 0 ? v[2] : mul2(v[2], bc2(-1.0f));
     }
     return r;
 }
@@ -304,122 +331,183 @@ template <int Q> __host__ __device__ constexpr bool pair_head(int q) {
 }
 
 template <int Q, int q>
-__device__ __forceinline__ void collide_pair(float* f, const float* u, const float* a, float base,
-                                             float ua, const CollK& k) {
+__device__ __forceinline__ void collide_pair2(float2* f, const float2* u, const float2* a, float2 base,
+                                              float2 nua, const CollK& k) {
     if constexpr (q < Q) {
         if constexpr (pair_head<Q>(q)) {
             using L = Lat<Q>;
             constexpr int qo = L::opp(q);
             constexpr int cls = (Q == 9 ? q >= 5 : q >= 7) ? 1 : 0;
-            const float cu = cdot<Q, q>(u), ca = cdot<Q, q>(a);
-            const float t = fmaf(1.5f * cu, cu, base);
-            const float eq = t + cu, eo = t - cu;                     // feq / A
-            const float Fq = fmaf(ca, fmaf(3.0f, cu, 1.0f), -ua);     // F / fA
-            const float Fo = fmaf(-ca, fmaf(-3.0f, cu, 1.0f), -ua);
-            f[q - 1] = fmaf(k.keep, f[q - 1], fmaf(k.omk, k.A[cls] * eq, k.fA[cls] * Fq));
-            f[qo - 1] = fmaf(k.keep, f[qo - 1], fmaf(k.omk, k.A[cls] * eo, k.fA[cls] * Fo));
+            const float2 cu = cdot2<Q, q>(u), ca = cdot2<Q, q>(a);
+            const float2 t = fma2(mul2(bc2(1.5f), cu), cu, base);
+            const float2 eq = add2(t, cu), eo = sub2(t, cu);                    // feq / A
+            const float2 Fq = fma2(ca, fma2(bc2(3.0f), cu, bc2(1.0f)), nua);    // F / fA
+            const float2 Fo = fma2(ca, fma2(bc2(3.0f), cu, bc2(-1.0f)), nua);   // (-c.a)(1 - 3 c.u) - u.a
+            f[q - 1] = fma2(bc2(k.keep), f[q - 1], fma2(bc2(k.omk), mul2(bc2(k.A[cls]), eq), mul2(bc2(k.fA[cls]), Fq)));
+            f[qo - 1] = fma2(bc2(k.keep), f[qo - 1], fma2(bc2(k.omk), mul2(bc2(k.A[cls]), eo), mul2(bc2(k.fA[cls]), Fo)));
         }
-        collide_pair<Q, q + 1>(f, u, a, base, ua, k);
+        collide_pair2<Q, q + 1>(f, u, a, base, nua, k);
     }
 }
 
-// Penalty source on a solid node, added to the post-collision f (which no
-// longer holds the pre-collision values: they are passed in fpre).
+// Penalty source on solid nodes (Eq. 17) in two parts: the non-equilibrium
+// momentum flux Pi_neq = sum_q (f_q - feq_q) c_q c_q of the pre-collision
+// populations (xx yy zz xy xz yz), taken before the collision overwrites f,
+// and S_q = 1.5 alpha A_q (c_q^T Pi c_q - tr(Pi)/3) added after it.
 template <int Q>
-__device__ __forceinline__ void add_penalty(float* f, const float* fpre, const float* u, float base,
-                                            float alpha) {
+__device__ __forceinline__ void pi_neq2(const float2* f, const float2* u, float2 base, float2* P) {
     using L = Lat<Q>;
-    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // xx yy zz xy xz yz of Pi_neq
+    bool set[6] = {false, false, false, false, false, false};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) P[i] = bc2(0.f);
+    auto acc = [&](int i, float2 v, bool neg) {
+        if (!set[i]) P[i] = neg ? mul2(v, bc2(-1.0f)) : v;
+        else P[i] = neg ? sub2(P[i], v) : add2(P[i], v);
+        set[i] = true;
+    };
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-        float cu = 0.f;
+        float2 cu = bc2(0.f);
+        bool first = true;
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if (L::c(q, d) != 0) cu += L::c(q, d) > 0 ? u[d] : -u[d];
-        const float fn = fpre[q - 1] - L::A(q) * fmaf(1.5f * cu, cu, base + cu);
+        for (int d = 0; d < 3; ++d) {
+            const int c = L::c(q, d);
+            if (c == 0) continue;
+            if (first) cu = c > 0 ? u[d] : mul2(u[d], bc2(-1.0f));
+            else cu = c > 0 ? add2(cu, u[d]) : sub2(cu, u[d]);
+            first = false;
+        }
+        const float2 fn = fma2(bc2(-L::A(q)), fma2(mul2(bc2(1.5f), cu), cu, add2(base, cu)), f[q - 1]);
         const int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
-        if (cx) P[0] += fn;
-        if (cy) P[1] += fn;
-        if (cz) P[2] += fn;
-        if (cx * cy) P[3] += cx * cy > 0 ? fn : -fn;
-        if (cx * cz) P[4] += cx * cz > 0 ? fn : -fn;
-        if (cy * cz) P[5] += cy * cz > 0 ? fn : -fn;
-    }
-    const float trP = (P[0] + P[1] + P[2]) * (1.0f / 3.0f);
-    const float sfac = 1.5f * alpha;
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
-        float pcc = 0.f;
-        if (cx) pcc += P[0];
-        if (cy) pcc += P[1];
-        if (cz) pcc += P[2];
-        if (cx * cy) pcc += 2.0f * (cx * cy > 0 ? P[3] : -P[3]);
-        if (cx * cz) pcc += 2.0f * (cx * cz > 0 ? P[4] : -P[4]);
-        if (cy * cz) pcc += 2.0f * (cy * cz > 0 ? P[5] : -P[5]);
-        f[q - 1] += sfac * L::A(q) * (pcc - trP);
+        if (cx) acc(0, fn, false);
+        if (cy) acc(1, fn, false);
+        if (cz) acc(2, fn, false);
+        if (cx * cy) acc(3, fn, cx * cy < 0);
+        if (cx * cz) acc(4, fn, cx * cz < 0);
+        if (cy * cz) acc(5, fn, cy * cz < 0);
     }
 }
 
-// Moments of the stored populations, written out without adding zeros.
 template <int Q>
-__device__ __forceinline__ void moments(const float* f, float& s, float* m) {
+__device__ __forceinline__ void add_penalty2(float2* f, const float2* P, bool solid0, bool solid1, const CollK& k) {
+    using L = Lat<Q>;
+    const float2 trP = mul2(add2(add2(P[0], P[1]), P[2]), bc2(1.0f / 3.0f));
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
+        float2 pcc = bc2(0.f);
+        bool first = true;
+        const int dia[3] = {cx, cy, cz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (!dia[d]) continue;
+            pcc = first ? P[d] : add2(pcc, P[d]);
+            first = false;
+        }
+        if (cx * cy) pcc = fma2(bc2(cx * cy > 0 ? 2.0f : -2.0f), P[3], pcc);
+        if (cx * cz) pcc = fma2(bc2(cx * cz > 0 ? 2.0f : -2.0f), P[4], pcc);
+        if (cy * cz) pcc = fma2(bc2(cy * cz > 0 ? 2.0f : -2.0f), P[5], pcc);
+        const int cls = (Q == 9 ? q >= 5 : q >= 7) ? 1 : 0;
+        const float2 fp = fma2(bc2(k.sA[cls]), sub2(pcc, trP), f[q - 1]);
+        f[q - 1] = make_float2(solid0 ? fp.x : f[q - 1].x, solid1 ? fp.y : f[q - 1].y);
+    }
+}
+
+// Moments of the stored populations of two nodes, without adding zeros.
+template <int Q>
+__device__ __forceinline__ void moments2(const float2* f, float2& s, float2* m) {
     if constexpr (Q == 9) {
-        const float d13 = f[0] - f[2], d24 = f[1] - f[3], d57 = f[4] - f[6], d68 = f[5] - f[7];
-        s = ((f[0] + f[2]) + (f[1] + f[3])) + ((f[4] + f[6]) + (f[5] + f[7]));
-        m[0] = d13 + (d57 - d68);
-        m[1] = d24 + (d57 + d68);
-        m[2] = 0.f;
+        const float2 d13 = sub2(f[0], f[2]), d24 = sub2(f[1], f[3]), d57 = sub2(f[4], f[6]),
+                     d68 = sub2(f[5], f[7]);
+        s = add2(add2(add2(f[0], f[2]), add2(f[1], f[3])), add2(add2(f[4], f[6]), add2(f[5], f[7])));
+        m[0] = add2(d13, sub2(d57, d68));
+        m[1] = add2(d24, add2(d57, d68));
+        m[2] = bc2(0.f);
     } else {
         // D3Q19 pairs (1,2) x, (3,4) y, (5,6) z, (7,8) xy, (9,10) x-y, (11,12) xz,
         // (13,14) x-z, (15,16) yz, (17,18) y-z; d_k = f_head - f_tail
-        const float dx = f[0] - f[1], dy = f[2] - f[3], dz = f[4] - f[5];
-        const float dxy = f[6] - f[7], dxmy = f[8] - f[9], dxz = f[10] - f[11];
-        const float dxmz = f[12] - f[13], dyz = f[14] - f[15], dymz = f[16] - f[17];
-        float a0 = 0.f, a1 = 0.f;
+        const float2 dx = sub2(f[0], f[1]), dy = sub2(f[2], f[3]), dz = sub2(f[4], f[5]);
+        const float2 dxy = sub2(f[6], f[7]), dxmy = sub2(f[8], f[9]), dxz = sub2(f[10], f[11]);
+        const float2 dxmz = sub2(f[12], f[13]), dyz = sub2(f[14], f[15]), dymz = sub2(f[16], f[17]);
+        float2 a0 = f[0], a1 = f[1];
 #pragma unroll
-        for (int i = 0; i < 18; i += 2) {
-            a0 += f[i];
-            a1 += f[i + 1];
+        for (int i = 2; i < 18; i += 2) {
+            a0 = add2(a0, f[i]);
+            a1 = add2(a1, f[i + 1]);
         }
-        s = a0 + a1;
-        m[0] = dx + ((dxy + dxmy) + (dxz + dxmz));
-        m[1] = dy + ((dxy - dxmy) + (dyz + dymz));
-        m[2] = dz + ((dxz - dxmz) + (dyz - dymz));
+        s = add2(a0, a1);
+        m[0] = add2(dx, add2(add2(dxy, dxmy), add2(dxz, dxmz)));
+        m[1] = add2(dy, add2(sub2(dxy, dxmy), add2(dyz, dymz)));
+        m[2] = add2(dz, add2(sub2(dxz, dxmz), sub2(dyz, dymz)));
     }
 }
 
-// One node: f holds the stored populations q = 1..Q-1 (index q-1) after
-// streaming; on return it holds f*.  u and p of Eq. 15 are returned.
+// Scalar moments (the adjoint's forward recomputation): the same sums.
 template <int Q>
-__device__ __forceinline__ void collide(float* f, const float* a, bool solid, const CollK& k,
-                                        float* u_out, float* p_out) {
+__device__ __forceinline__ void moments(const float* f, float& s, float* m) {
+    float2 f2v[Q - 1];
+#pragma unroll
+    for (int q = 0; q < Q - 1; ++q) f2v[q] = bc2(f[q]);
+    float2 s2, m2[3];
+    moments2<Q>(f2v, s2, m2);
+    s = s2.x;
+    m[0] = m2[0].x;
+    m[1] = m2[1].x;
+    m[2] = m2[2].x;
+}
+
+// Two nodes: f holds the stored populations q = 1..Q-1 (index q-1) after
+// streaming; on return it holds f*.  u and p of Eq. 15 are returned.  solid
+// flags the halves on which the penalty acts.
+template <int Q>
+__device__ __forceinline__ void collide2(float2* f, const float2* a, bool solid0, bool solid1, const CollK& k,
+                                         float2* u_out, float2* p_out) {
     using L = Lat<Q>;
     constexpr int D = L::D;
     constexpr float inv_sa = (float)(1.0 / L::SUMA);
     constexpr float kuu = (float)(1.5 - 0.5 * L::SUMA);
-    float s, m[3];
-    moments<Q>(f, s, m);
-    float u[3];
-    u[0] = fmaf(0.5f, a[0], m[0]);  // Eq. 15a
-    u[1] = fmaf(0.5f, a[1], m[1]);
-    u[2] = D == 3 ? fmaf(0.5f, a[2], m[2]) : 0.f;
-    const float uu = D == 3 ? fmaf(u[2], u[2], fmaf(u[1], u[1], u[0] * u[0])) : fmaf(u[1], u[1], u[0] * u[0]);
-    const float p = fmaf(-kuu, uu, s) * inv_sa;  // Eq. 15b
-    const float ua = D == 3 ? fmaf(u[2], a[2], fmaf(u[1], a[1], u[0] * a[0])) : fmaf(u[1], a[1], u[0] * a[0]);
-    const float base = fmaf(-0.5f, uu, p);
+    float2 s, m[3];
+    moments2<Q>(f, s, m);
+    float2 u[3];
+    u[0] = fma2(bc2(0.5f), a[0], m[0]);  // Eq. 15a
+    u[1] = fma2(bc2(0.5f), a[1], m[1]);
+    u[2] = D == 3 ? fma2(bc2(0.5f), a[2], m[2]) : bc2(0.f);
+    const float2 uu = D == 3 ? fma2(u[2], u[2], fma2(u[1], u[1], mul2(u[0], u[0])))
+                             : fma2(u[1], u[1], mul2(u[0], u[0]));
+    const float2 p = mul2(fma2(bc2(-kuu), uu, s), bc2(inv_sa));  // Eq. 15b
+    const float2 ua = D == 3 ? fma2(u[2], a[2], fma2(u[1], a[1], mul2(u[0], a[0])))
+                             : fma2(u[1], a[1], mul2(u[0], a[0]));
+    const float2 nua = mul2(ua, bc2(-1.0f));
+    const float2 base = fma2(bc2(-0.5f), uu, p);
 #pragma unroll
     for (int d = 0; d < 3; ++d) u_out[d] = u[d];
     *p_out = p;
-    if (solid) {
-        float fpre[Q - 1];
-#pragma unroll
-        for (int q = 0; q < Q - 1; ++q) fpre[q] = f[q];
-        collide_pair<Q, 1>(f, u, a, base, ua, k);
-        add_penalty<Q>(f, fpre, u, base, k.alpha);
+    if (solid0 || solid1) {
+        float2 P[6];
+        pi_neq2<Q>(f, u, base, P);
+        collide_pair2<Q, 1>(f, u, a, base, nua, k);
+        add_penalty2<Q>(f, P, solid0, solid1, k);
     } else {
-        collide_pair<Q, 1>(f, u, a, base, ua, k);
+        collide_pair2<Q, 1>(f, u, a, base, nua, k);
     }
+}
+
+// One node (both halves of the packed arithmetic carry it): the same bits
+// as collide2 gives that node.
+template <int Q>
+__device__ __forceinline__ void collide(float* f, const float* a, bool solid, const CollK& k, float* u_out,
+                                        float* p_out) {
+    float2 f2v[Q - 1], a2[3], u2[3], p2;
+#pragma unroll
+    for (int q = 0; q < Q - 1; ++q) f2v[q] = bc2(f[q]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a2[d] = bc2(a[d]);
+    collide2<Q>(f2v, a2, solid, solid, k, u2, &p2);
+#pragma unroll
+    for (int q = 0; q < Q - 1; ++q) f[q] = f2v[q].x;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u_out[d] = u2[d].x;
+    *p_out = p2.x;
 }
 
 // Exact fixed-point image round(u * 2^FXBITS) of a velocity component, with

@@ -216,31 +216,40 @@ __device__ __forceinline__ void fluid_tile(const InstDesc& in, int local, int pa
         }
         int slot[V];
         float uv[3][V];
+        // nodes in pairs: packed FP32x2 collision (same bits as the TMA path)
+        constexpr int PAIR = V >= 2 ? 2 : 1;
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int xyz[3] = {xl + e, y, z};
-            const bool valid = active && (xl + e < in.n[0]);
-            int own = -1, sl = -1;
-            if (ncand > 0) own = owner_of<D>(geo, cand, ncand, xyz, &sl);
-            float a[3] = {in.gdrive[0], in.gdrive[1], in.gdrive[2]};
-            if (own >= 0) {
+        for (int e = 0; e < V; e += PAIR) {
+            int own[2] = {-1, -1}, sl[2] = {-1, -1};
+            float2 a2[3], f2v[QS], u2[3], p2;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) a[d] += cand[sl].a[d];
+            for (int h = 0; h < 2; ++h) {
+                const int ee = PAIR == 2 ? e + h : e;
+                const int xyz[3] = {xl + ee, y, z};
+                if (ncand > 0) own[h] = owner_of<D>(geo, cand, ncand, xyz, &sl[h]);
             }
-            float fn[QS];
 #pragma unroll
-            for (int q = 0; q < QS; ++q) fn[q] = f[q][e];
-            float u[3], p;
-            collide<Q>(fn, a, own >= 0, ck, u, &p);
+            for (int d = 0; d < 3; ++d)
+                a2[d] = add2(bc2(in.gdrive[d]), make_float2(own[0] >= 0 ? cand[sl[0]].a[d] : 0.f,
+                                                            own[1] >= 0 ? cand[sl[1]].a[d] : 0.f));
 #pragma unroll
-            for (int q = 0; q < QS; ++q) f[q][e] = fn[q];
-            float uu = 0.f;
+            for (int q = 0; q < QS; ++q) f2v[q] = make_float2(f[q][e], f[q][PAIR == 2 ? e + 1 : e]);
+            collide2<Q>(f2v, a2, own[0] >= 0, own[1] >= 0, ck, u2, &p2);
 #pragma unroll
-            for (int d = 0; d < D; ++d) uu = fmaf(u[d], u[d], uu);
-            if (valid && !(uu < 0.25f)) bad = true;
-            slot[e] = valid ? sl : -1;
+            for (int h = 0; h < PAIR; ++h) {
+                const int ee = e + h;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) uv[d][e] = d < D ? u[d] : 0.f;
+                for (int q = 0; q < QS; ++q) f[q][ee] = h ? f2v[q].y : f2v[q].x;
+                const float u[3] = {h ? u2[0].y : u2[0].x, h ? u2[1].y : u2[1].x, h ? u2[2].y : u2[2].x};
+                float uu = 0.f;
+#pragma unroll
+                for (int d = 0; d < D; ++d) uu = fmaf(u[d], u[d], uu);
+                const bool valid = active && (xl + ee < in.n[0]);
+                if (valid && !(uu < 0.25f)) bad = true;
+                slot[ee] = valid ? sl[h] : -1;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) uv[d][ee] = d < D ? u[d] : 0.f;
+            }
         }
         if (active) {
             const long long off = ((long long)z * in.n[1] + y) * in.pitch + xl;

@@ -129,10 +129,10 @@ __host__ __device__ inline TmaLayout tma_layout(int Q, int ssize, int tw, int ro
     return L;
 }
 
-// Register budget: D2Q9 fits three blocks of 9 warps per SM without spills,
-// D3Q19 two.
+// Register budget: two blocks of 9 warps per SM (the shared-memory ring of
+// three stages allows no more); each lane collides two nodes at a time.
 template <int Q, class S, int TW, int ROWS>
-__global__ void __launch_bounds__(288, (Q == 9 ? 3 : 2)) k_fluid_tma(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict__ insts,
                                                    const CUtensorMap* __restrict__ tmaps,
                                                    const uint16_t* __restrict__ tile_inst, int ntiles,
                                                    int par, Shape sh, int commit, int* tile_ctr,
@@ -309,62 +309,84 @@ __global__ void __launch_bounds__(288, (Q == 9 ? 3 : 2)) k_fluid_tma(const InstD
             const bool rowfast = rowok == (((1u << Q) - 1) & ~1u);
             const S* rowbase = stage + r * BW + H;
             S* outrow = static_cast<S*>(h.fout) + ((long long)z * ny + y) * h.pitch;
-            for (int j = 0; j < TW / 32; ++j) {
-                const int lx = j * 32 + lane;
+            // two adjacent nodes per lane: packed FP32x2 arithmetic, 8-byte stores
+            for (int j = 0; j < TW / 64; ++j) {
+                const int lx = j * 64 + 2 * lane;
                 const int x = x0 + lx;
-                const bool valid = x < nx;
-                float f[QS];
-                if (rowfast && __all_sync(0xffffffffu, x > 0 && x < nx - 1)) {
+                const bool v0 = x < nx, v1 = x + 1 < nx;
+                float2 f[QS];
+                if (rowfast && __all_sync(0xffffffffu, x > 0 && x + 1 < nx - 1)) {
 #pragma unroll
-                    for (int q = 1; q < Q; ++q)
-                        f[q - 1] = to_float_scaled(rowbase[(q - 1) * SLAB + lx - L::c(q, 0)], h.sload);
+                    for (int q = 1; q < Q; ++q) {
+                        const S* src = rowbase + (q - 1) * SLAB + lx - L::c(q, 0);
+                        if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, h.sload);
+                        else f[q - 1] = make_float2(to_float_scaled(src[0], h.sload), to_float_scaled(src[1], h.sload));
+                    }
                 } else {
 #pragma unroll
                     for (int q = 1; q < Q; ++q) {
                         const int cx = L::c(q, 0);
-                        if (((rowok >> q) & 1u) && x - cx >= 0 && x - cx < nx)
-                            f[q - 1] = to_float_scaled(rowbase[(q - 1) * SLAB + lx - cx], h.sload);
-                        else
-                            f[q - 1] = valid ? pull_scalar<Q, S>(insts[h.inst], static_cast<const S*>(h.fin),
-                                                                  q, x, y, z)
-                                             : 0.f;
+                        float v[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int xe = x + e;
+                            if (((rowok >> q) & 1u) && xe - cx >= 0 && xe - cx < nx)
+                                v[e] = to_float_scaled(rowbase[(q - 1) * SLAB + lx + e - cx], h.sload);
+                            else
+                                v[e] = xe < nx ? pull_scalar<Q, S>(insts[h.inst], static_cast<const S*>(h.fin), q, xe,
+                                                                     y, z)
+                                               : 0.f;
+                        }
+                        f[q - 1] = make_float2(v[0], v[1]);
                     }
                 }
-                const int xyz[3] = {x, y, z};
-                int own = -1, sl = -1;
+                const int xyz0[3] = {x, y, z}, xyz1[3] = {x + 1, y, z};
+                int own0 = -1, own1 = -1, sl0 = -1, sl1 = -1;
                 unsigned act = 0;
                 if (ncand > 32) {  // more candidates than mask bits: test them all
                     act = 0xffffffffu;
-                    own = owner_of<D>(geo, cand, ncand, xyz, &sl);
+                    own0 = owner_of<D>(geo, cand, ncand, xyz0, &sl0);
+                    own1 = owner_of<D>(geo, cand, ncand, xyz1, &sl1);
                 } else if (ncand > 0) {
-                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 32, y, z);
-                    if (act) own = owner_masked<D>(geo, cand, act, xyz, &sl);
+                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 64, y, z, 64);
+                    if (act) {
+                        own0 = owner_masked<D>(geo, cand, act, xyz0, &sl0);
+                        own1 = owner_masked<D>(geo, cand, act, xyz1, &sl1);
+                    }
                 }
-                float a[3] = {h.gdrive[0], h.gdrive[1], h.gdrive[2]};
-                if (own >= 0) {
+                float2 a[3];
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) a[d] += cand[sl].a[d];
-                }
-                float u[3], p;
-                collide<Q>(f, a, own >= 0, h.ck, u, &p);
-                float uu = 0.f;
+                for (int d = 0; d < 3; ++d)
+                    a[d] = add2(bc2(h.gdrive[d]),
+                                make_float2(own0 >= 0 ? cand[sl0].a[d] : 0.f, own1 >= 0 ? cand[sl1].a[d] : 0.f));
+                float2 u[3], p;
+                collide2<Q>(f, a, own0 >= 0, own1 >= 0, h.ck, u, &p);
+                float2 uu = mul2(u[0], u[0]);
 #pragma unroll
-                for (int d = 0; d < D; ++d) uu = fmaf(u[d], u[d], uu);
-                if (valid) {
-                    bad |= !(uu < 0.25f);
+                for (int d = 1; d < D; ++d) uu = fma2(u[d], u[d], uu);
+                bad |= (v0 && !(uu.x < 0.25f)) || (v1 && !(uu.y < 0.25f));
+                if (v0) {
                     S* o = outrow + x;
                     const int qs = (int)h.qstride;  // < 2^31 elements per population
                     const float sstore = h.sstore;
+                    if (v1) {
 #pragma unroll
-                    for (int q = 0; q < QS; ++q) {
-                        *o = to_store<S>(f[q], sstore);
-                        o += qs;
+                        for (int q = 0; q < QS; ++q) {
+                            store_pair(o, f[q], sstore);
+                            o += qs;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < QS; ++q) {
+                            *o = to_store<S>(f[q].x, sstore);
+                            o += qs;
+                        }
                     }
                 }
                 if (act) {
-                    const int slot[1] = {valid ? sl : -1};
-                    const float uv[3][1] = {{u[0]}, {u[1]}, {D == 3 ? u[2] : 0.f}};
-                    row_partials<D, 1>(geo, cand, ncand, h.partial, h.maxk, slot, uv, x, y, z, lane);
+                    const int slot[2] = {v0 ? sl0 : -1, v1 ? sl1 : -1};
+                    const float uv[3][2] = {{u[0].x, u[0].y}, {u[1].x, u[1].y}, {D == 3 ? u[2].x : 0.f, D == 3 ? u[2].y : 0.f}};
+                    row_partials<D, 2>(geo, cand, ncand, h.partial, h.maxk, slot, uv, x, y, z, lane);
                 }
             }
         }
