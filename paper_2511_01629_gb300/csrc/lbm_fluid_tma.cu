@@ -1,18 +1,20 @@
 // TMA-pipelined variant of the fused stream-collide-penalize kernel.
 //
 // Persistent blocks of one producer warp and NC consumer warps.  The producer
-// takes tiles from a work counter, stages the tile's candidate particles in
-// shared memory and issues one cp.async.bulk.tensor box per stored population:
-// the source rows (y - c_y, z - c_z) of the tile, 32*k nodes wide plus a
-// 16-byte halo on both sides so that every box starts on a 16-byte boundary.
-// The boxes of a tile land in one stage of a ring of shared-memory buffers,
-// counted by an mbarrier; the consumers pull each node's populations from
-// shared memory at x - c_x (conflict-free, one node per lane), collide, store
-// to HBM with coalesced stores, and reduce the per-particle sums of Eq. 22.
-// Bytes in flight live in shared memory instead of registers, which keeps
-// HBM busy with few threads.  Rows whose source lies beyond a face (walls or
-// periodic wrap) and the nodes x = 0, nx - 1 read those populations from HBM
-// directly (bounce-back, wrap), as the register-path kernel does.
+// takes tiles from a work counter (claimed one tile ahead) and issues one
+// cp.async.bulk.tensor box per stored population: the source rows
+// (y - c_y, z - c_z) of the tile, 32*k nodes wide plus a 16-byte halo on both
+// sides so that every box starts on a 16-byte boundary; while the copies are
+// in flight it stages the tile's header and candidate particles.  The boxes
+// of a tile land in one stage of a ring of shared-memory buffers, counted by
+// an mbarrier; each consumer lane pulls two adjacent nodes' populations from
+// shared memory at x - c_x, collides them with packed FP32x2 arithmetic,
+// stores them to HBM with 8-byte coalesced stores, and reduces the
+// per-particle sums of Eq. 22.  Bytes in flight live in shared memory instead
+// of registers, which keeps HBM busy with few threads.  Rows whose source
+// lies beyond a face (walls or periodic wrap) and the nodes x = 0, nx - 1 read
+// those populations from HBM directly (bounce-back, wrap), as the
+// register-path kernel does.
 //
 // Every mbarrier wait is bounded in time; on expiry the kernel records a
 // timeout in the status word, waits (bounded) for the copies it issued and
@@ -31,8 +33,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+// Raise the bytes the current phase waits for, without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -167,6 +170,10 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         // ---------------------------------------------------------- producer
         bool ok = true;
         int issued = 0;
+        // tiles from a work counter, claimed one iteration ahead so that the
+        // atomic's latency hides behind the current tile's staging
+        int t_next = 0;
+        if (lane == 0) t_next = atomicAdd(&tile_ctr[0], 1);
         for (int it = 0;; ++it) {
             const int s = it % stages;
             const uint32_t ph = (uint32_t)(it / stages) & 1u;
@@ -174,9 +181,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 ok = false;
                 break;
             }
-            int t = 0;
-            if (lane == 0) t = atomicAdd(&tile_ctr[0], 1);
-            t = __shfl_sync(0xffffffffu, t, 0);
+            const int t = __shfl_sync(0xffffffffu, t_next, 0);
             if (t >= ntiles) {
                 if (lane == 0) {
                     hdr[s].tile = -1;
@@ -190,6 +195,24 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
             const int ntx = in.ntile[0], nty = in.ntile[1];
             const int x0 = (local % ntx) * TW, rest = local / ntx;
             const int y0 = (rest % nty) * sh.ty, z0 = (rest / nty) * sh.tz;
+            if (lane == 0) t_next = atomicAdd(&tile_ctr[0], 1);
+            // the copies go out first; the tile's header and candidates are
+            // staged while they are in flight, and the arrive that completes the
+            // phase follows them
+            if (lane == 0) {
+                const CUtensorMap* map = tmaps + 2 * ii + par;
+                mbar_expect_tx(&full[s], (uint32_t)(QS * LY.bw * rows * (int)sizeof(S)));
+                unsigned char* dst = smem + s * LY.stage;
+#pragma unroll 1
+                for (int q = 1; q < Q; ++q) {
+                    const int cy = Q == 9 ? d2q9_c(q, 1) : d3q19_c(q, 1);
+                    const int cz = Q == 9 ? 0 : d3q19_c(q, 2);
+                    if (D == 2)
+                        tma_load_3d(dst + (q - 1) * LY.slab, map, x0 - H, y0 - cy, q - 1, &full[s]);
+                    else
+                        tma_load_4d(dst + (q - 1) * LY.slab, map, x0 - H, y0 - cy, z0 - cz, q - 1, &full[s]);
+                }
+            }
             int ncand = 0;
             if (in.np > 0) {
                 ncand = min(in.list_cnt[par][local], LIST_CAP);
@@ -235,24 +258,11 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 h.partial = commit ? in.partial : in.partial_scratch;
                 h.prec = in.prec;
                 h.status = in.status;
+                h.tile = t;
+                h.ncand = ncand;
             }
-            __syncwarp();
-            if (lane == 0) {
-                hdr[s].tile = t;
-                hdr[s].ncand = ncand;
-                const CUtensorMap* map = tmaps + 2 * ii + par;
-                mbar_arrive_expect_tx(&full[s], (uint32_t)(QS * LY.bw * rows * (int)sizeof(S)));
-                unsigned char* dst = smem + s * LY.stage;
-#pragma unroll 1
-                for (int q = 1; q < Q; ++q) {
-                    const int cy = Q == 9 ? d2q9_c(q, 1) : d3q19_c(q, 1);
-                    const int cz = Q == 9 ? 0 : d3q19_c(q, 2);
-                    if (D == 2)
-                        tma_load_3d(dst + (q - 1) * LY.slab, map, x0 - H, y0 - cy, q - 1, &full[s]);
-                    else
-                        tma_load_4d(dst + (q - 1) * LY.slab, map, x0 - H, y0 - cy, z0 - cz, q - 1, &full[s]);
-                }
-            }
+            __syncwarp();  // the lanes' candidate records are visible to lane 0's arrive
+            if (lane == 0) mbar_arrive(&full[s]);
             ++issued;
         }
         if (!ok) {
