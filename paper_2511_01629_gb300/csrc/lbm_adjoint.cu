@@ -486,7 +486,9 @@ __global__ void __launch_bounds__(128) k_adj_particles(const InstDesc* __restric
                                                        const AdjPart* __restrict__ steps,
                                                        const AdjBufs* __restrict__ bufs) {
     const int ii = blockIdx.x;
-    const InstDesc& in = insts[ii];
+    __shared__ __align__(16) InstDesc sdesc;
+    stage_desc(&sdesc, insts[ii]);
+    const InstDesc& in = sdesc;
     const int np = in.np;
     if (np == 0) return;
     const AdjPart sp = steps[ii];

@@ -6,6 +6,17 @@
 
 namespace lbmpen {
 
+// Block-wide copy of an instance descriptor into shared memory: one coalesced
+// round trip instead of a dependent global load for every field the serial
+// per-particle code touches.  Ends with __syncthreads().
+__device__ __forceinline__ void stage_desc(InstDesc* dst, const InstDesc& src) {
+    static_assert(sizeof(InstDesc) % 8 == 0, "descriptor copied in 8-byte words");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(&src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(InstDesc) / 8); i += blockDim.x) d[i] = __ldg(s + i);
+    __syncthreads();
+}
+
 // ------------------------------------------------------------ vector I/O ---
 template <class S, int V> struct VecIO;
 

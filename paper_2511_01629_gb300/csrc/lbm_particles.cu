@@ -23,13 +23,10 @@ constexpr int XCHUNK = 1024;  // particle positions staged in shared memory at a
 // a particle by |h Ubar| < 1/2) leaves only pairs near the interaction range
 // for the FP64 evaluation, which follows the reference operation order.
 __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lane, const float4* xs,
-                           const float4* xs2, int j0, int nj, double* f1, double* f2) {
+                           const float4* xs2, int j0, int nj, float4 xi, float4 xi2, double cp,
+                           double inv_delta, double* f1, double* f2) {
     const double* Xb = in.Xk + (long long)src * in.np * 3;
-    const double cp = in.pconst[PCONST_N * i + PC_CPAIR];  // C / eps_p of particle i
-    if (cp == 0.0) return;
-    const double inv_delta = in.pconst[PCONST_N * i + PC_INVDELTA];
-    const float4 xi = reinterpret_cast<const float4*>(in.Xf)[(long long)src * in.np + i];
-    const float4 xi2 = reinterpret_cast<const float4*>(in.Xsf)[(long long)src * in.np + i];
+    if (cp == 0.0) return;  // cp = C / eps_p of particle i
     const float reach = xi.w + (float)in.delta + 0.01f;  // FP32 positions carry < 1e-3 error
     const float nf[3] = {(float)in.n[0], (float)in.n[1], (float)in.n[2]};
     const bool per[3] = {in.periodic[0] && in.n[0] > 1, in.periodic[1] && in.n[1] > 1,
@@ -94,11 +91,10 @@ __device__ void gather_pairs(const double* f1, const double* f2, double* F1, dou
 }
 
 // Wall part of Eq. 21 (mirror images across the planes -1/2 and n - 1/2).
-__device__ void wall_force(const InstDesc& in, int i, const double* Xi, double* F) {
-    const double cw = in.pconst[PCONST_N * i + PC_CWALL];  // C / eps_w of particle i
-    if (cw == 0.0) return;
-    const double inv_delta = in.pconst[PCONST_N * i + PC_INVDELTA];
-    const float reach = 0.5f * (2.0f * (float)in.R[i] + (float)in.delta) + 0.01f;
+__device__ void wall_force(const InstDesc& in, const double* Xi, double* F, double cw, double inv_delta,
+                           double Ri) {
+    if (cw == 0.0) return;  // cw = C / eps_w of the particle
+    const float reach = 0.5f * (2.0f * (float)Ri + (float)in.delta) + 0.01f;
     for (int d = 0; d < 3; ++d) {
         if (in.periodic[d] || in.n[d] <= 1) continue;
         const float xf = (float)Xi[d];  // skip walls farther than (2R + delta)/2
@@ -108,7 +104,7 @@ __device__ void wall_force(const InstDesc& in, int i, const double* Xi, double* 
             const double Xim = 2.0 * walls[face] - Xi[d];
             const double diff = Xi[d] - Xim;
             const double dprime = fabs(diff);
-            const double range = 2.0 * in.R[i] + in.delta;
+            const double range = 2.0 * Ri + in.delta;
             if (dprime <= range) {
                 const double sc = (range - dprime) * inv_delta;
                 F[d] += cw * diff * sc * sc;
@@ -172,20 +168,20 @@ __device__ __forceinline__ int axis_tile(const AxisTiles& t, int i) {
 // Record of particle p at its current X and A for the next fluid step, and
 // the tiles of its bounding box (slots k enumerate them x-fastest; no tile is
 // listed twice).  One thread.
-__device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at) {
-    const double R = in.pconst[PCONST_N * p + PC_R];
+// Record of particle p from its new state (X, A) and constants (R, 1 - rho_f/rho_s).
+__device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at,
+                                 const double* Xp, const double* Ap, double R, float gfac) {
     const float Rf = (float)R;
     const int T[3] = {sh.tw, sh.ty, sh.tz};
     int cnt[3];
     PRec pr;
-    const float gfac = (float)in.pconst[PCONST_N * p + PC_GFAC];  // 1 - rho_f / rho_s
     for (int d = 0; d < 3; ++d) {
-        const double X = in.X[3 * p + d];
+        const double X = Xp[d];
         pr.X[d] = X;
         const int ref = d < D ? __double2int_rd(X) : 0;
         pr.ref[d] = ref;
         pr.frac[d] = (float)(X - (double)ref);
-        pr.a[d] = fmaf(gfac, in.ggrav[d], (float)in.A[3 * p + d]);
+        pr.a[d] = fmaf(gfac, in.ggrav[d], (float)Ap[d]);
         // box [X - R - 1, X + R + 1]: its one-node margin covers the float rounding
         at[d] = d >= D ? AxisTiles{0, 1, 0, 0}
                        : axis_tiles_f((float)ref + pr.frac[d], Rf, in.n[d], T[d], in.ntile[d], in.periodic[d]);
@@ -200,6 +196,16 @@ __device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, A
     pr.pad = 0;
     in.prec_out[p] = pr;
     if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
+}
+
+__device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at) {
+    double X[3], A[3];
+    for (int d = 0; d < 3; ++d) {
+        X[d] = in.X[3 * p + d];
+        A[d] = in.A[3 * p + d];
+    }
+    make_record_from(in, p, D, sh, at, X, A, in.pconst[PCONST_N * p + PC_R],
+                     (float)in.pconst[PCONST_N * p + PC_GFAC]);
 }
 
 // List entries of particle p in the tiles of its bounding box (lanes share).
@@ -226,27 +232,37 @@ __device__ void update_particle(const InstDesc& in, int i, const double* F1in, c
                                 int src, double h, int last, int D, const Shape& sh, AxisTiles* at) {
     const int dst = src ^ 1;
     const double* Xs = in.Xk + (long long)src * in.np * 3;
-    // operands up front: their loads overlap instead of following the FP64 chain
-    double X0[3], Ub[3], Xold[3], F1[3], F2[3];
+    // every operand up front, in one batch of loads: the FP64 chain below then
+    // runs without further round trips to memory
+    double X0[3], Ub[3], Xold[3], F1[3], F2[3], Wn[3], Un[3], Wo[3], Th[3];
     for (int d = 0; d < 3; ++d) {
         X0[d] = Xs[3 * i + d];
         Ub[d] = in.Ubar[3 * i + d];
         Xold[d] = in.X[3 * i + d];
         F1[d] = F1in[d];
         F2[d] = F2in[d];
+        Wn[d] = in.Wn[3 * i + d];
+        Un[d] = in.Un[3 * i + d];
+        Wo[d] = in.W[3 * i + d];
+        Th[d] = in.theta[3 * i + d];
     }
-    const double invM = in.pconst[PCONST_N * i + PC_INVRHOS] * in.invc[i];  // 1 / (rho_s n)
+    const double* pc = in.pconst + PCONST_N * i;
+    const double invrhos = pc[PC_INVRHOS], cw = pc[PC_CWALL], idl = pc[PC_INVDELTA], Ri = pc[PC_R];
+    const double gfac = pc[PC_GFAC];
+    const double invc = in.invc[i];
+    const int cnt = in.count[i];
+    const double invM = invrhos * invc;  // 1 / (rho_s n)
     double Xst[3];
     for (int d = 0; d < 3; ++d) Xst[d] = fma(h, Ub[d], X0[d]);
-    wall_force(in, i, X0, F1);
-    wall_force(in, i, Xst, F2);
+    wall_force(in, X0, F1, cw, idl, Ri);
+    wall_force(in, Xst, F2, cw, idl, Ri);
     const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
     double Xn[3];
     for (int d = 0; d < 3; ++d) Xn[d] = Xst[d] + c * (F1[d] + F2[d]);
     if (!last) {
         double* Xd = in.Xk + (long long)dst * in.np * 3;
         for (int d = 0; d < 3; ++d) Xd[3 * i + d] = Xn[d];
-        const float Rf = (float)in.pconst[PCONST_N * i + PC_R];
+        const float Rf = (float)Ri;
         reinterpret_cast<float4*>(in.Xf)[(long long)dst * in.np + i] =
             make_float4((float)Xn[0], (float)Xn[1], (float)Xn[2], Rf);
         reinterpret_cast<float4*>(in.Xsf)[(long long)dst * in.np + i] =
@@ -254,9 +270,9 @@ __device__ void update_particle(const InstDesc& in, int i, const double* F1in, c
         return;
     }
     bool left = false;
+    double An[3], Xw[3], Tn[3];
     for (int d = 0; d < 3; ++d) {
-        const int j = 3 * i + d;
-        in.A[j] = 2.0 * (Xn[d] - Xold[d] - Ub[d]);
+        An[d] = 2.0 * (Xn[d] - Xold[d] - Ub[d]);
         double xn = Xn[d];
         if (d < D) {
             if (in.periodic[d]) {
@@ -266,25 +282,28 @@ __device__ void update_particle(const InstDesc& in, int i, const double* F1in, c
                 left = true;
             }
         }
+        Xw[d] = xn;
+        Tn[d] = Th[d] + 0.5 * (Wn[d] + Wo[d]);
+        const int j = 3 * i + d;
+        in.A[j] = An[d];
         in.X[j] = xn;
-        const double wn = in.Wn[j], un = in.Un[j];
-        in.theta[j] += 0.5 * (wn + in.W[j]);
-        in.U[j] = un;
-        in.W[j] = wn;
+        in.theta[j] = Tn[d];
+        in.U[j] = Un[d];
+        in.W[j] = Wn[d];
     }
     if (left) atomicOr(in.status, ST_PARTICLE);
     if (in.rec_state) {  // adjoint recording: the state this step hands to the next
         double* r = in.rec_state + 16LL * i;
         for (int d = 0; d < 3; ++d) {
-            r[d] = in.X[3 * i + d];
-            r[3 + d] = in.U[3 * i + d];
-            r[6 + d] = in.W[3 * i + d];
-            r[9 + d] = in.theta[3 * i + d];
-            r[12 + d] = in.A[3 * i + d];
+            r[d] = Xw[d];
+            r[3 + d] = Un[d];
+            r[6 + d] = Wn[d];
+            r[9 + d] = Tn[d];
+            r[12 + d] = An[d];
         }
-        r[15] = (double)in.count[i];
+        r[15] = (double)cnt;
     }
-    make_record(in, i, D, sh, at);
+    make_record_from(in, i, D, sh, at, Xw, An, Ri, (float)gfac);
 }
 
 // ------------------------------------------------------------- the kernel --
@@ -300,6 +319,10 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // all resident).  Bounded: after PWAIT_NS it records a timeout and returns
 // false, and the kernel stops.
 __device__ bool grid_sync(GridBar* gb, int* status) {
+    if (gridDim.x == 1) {  // one block: the block barrier is the grid barrier
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
@@ -382,6 +405,14 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
     }
     const float4* Xfb = reinterpret_cast<const float4*>(in.Xf) + (long long)src * in.np;
     const float4* Xsb = reinterpret_cast<const float4*>(in.Xsf) + (long long)src * in.np;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), xi2 = xi;
+    double cp = 0.0, idl = 0.0;
+    if (mine) {  // issued before the staging barrier, so the loads overlap it
+        xi = Xfb[i];
+        xi2 = Xsb[i];
+        cp = in.pconst[PCONST_N * i + PC_CPAIR];
+        idl = in.pconst[PCONST_N * i + PC_INVDELTA];
+    }
     for (int j0 = 0; j0 < in.np; j0 += XCHUNK) {
         const int nj = min(XCHUNK, in.np - j0);
         __syncthreads();
@@ -390,7 +421,7 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
             xs2[k] = Xsb[j0 + k];
         }
         __syncthreads();
-        if (mine) pair_chunk(in, i, src, h, lane, xs, xs2, j0, nj, f1, f2);
+        if (mine) pair_chunk(in, i, src, h, lane, xs, xs2, j0, nj, xi, xi2, cp, idl, f1, f2);
     }
     if (mine) {
         double F1[3], F2[3];
@@ -421,7 +452,9 @@ __global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ 
     __shared__ float4 xs[XCHUNK];
     __shared__ float4 xs2[XCHUNK];
     const int gp0 = blockIdx.x * PB;
-    const InstDesc& in = insts[refs[gp0].inst];  // blocks never straddle instances
+    __shared__ __align__(16) InstDesc sdesc;
+    stage_desc(&sdesc, insts[refs[gp0].inst]);  // blocks never straddle instances
+    const InstDesc& in = sdesc;
     for (int ph = first; ph <= last; ++ph) {
         if (ph > first && !grid_sync(gb, in.status)) return;
         if (ph == 0) phase_finalize(in, refs, ntotal, D, gp0, tot);
