@@ -538,6 +538,19 @@ __device__ __forceinline__ long long to_fx(float u) {
     return b < 0 ? -v : v;
 }
 
+// Exact warp sum of a 64-bit integer of magnitude below 2^51: three 21-bit
+// limbs, each summed by one integer reduction (32 lanes keep every limb sum
+// below 2^26), recombined exactly.
+__device__ __forceinline__ long long warp_sum_fx(long long v) {
+    const unsigned l0 = (unsigned)(v & 0x1FFFFF);
+    const unsigned l1 = (unsigned)((v >> 21) & 0x1FFFFF);
+    const int l2 = (int)(v >> 42);  // arithmetic shift: the signed top limb
+    const long long s0 = (long long)__reduce_add_sync(0xffffffffu, l0);
+    const long long s1 = (long long)__reduce_add_sync(0xffffffffu, l1);
+    const long long s2 = (long long)__reduce_add_sync(0xffffffffu, l2);
+    return s0 + s1 * (1LL << 21) + s2 * (1LL << 42);
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -589,8 +602,8 @@ __device__ __forceinline__ void row_partials(const Geo& in, const Cand* cand, in
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v[10 + k] = (k < D) ? warp_sum_ll(su[k]) : 0;
-            v[13 + k] = (D == 3 || k == 2) ? warp_sum_ll(sl[k]) : 0;
+            v[10 + k] = (k < D) ? warp_sum_fx(su[k]) : 0;
+            v[13 + k] = (D == 3 || k == 2) ? warp_sum_fx(sl[k]) : 0;
         }
         if (lane == 0) {
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(
