@@ -41,6 +41,17 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (a time): every rank gets it."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workloads(name, seed):
     from paper_2511_01629_gb300 import workloads as W
     if name == "many_disks":
@@ -265,6 +276,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fp16-leg", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the batched-ensemble and D3Q19 lines")
     ap.add_argument("--adjoint-steps", type=int, default=5000)
     ap.add_argument("--shape", default=None,
                     help="fluid kernel shape vec,rows,warps (vec 0 = TMA pipeline) instead of autotuning")
@@ -320,11 +333,7 @@ def main():
             torch.cuda.synchronize()
             barrier()
         sim.sync()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         out.update(ms=ms, clocks=clk.summary())
         if with_kernel:
             # the dominant kernel alone, same stream, averaged over launches
@@ -362,6 +371,44 @@ def main():
                           "steps": ke, "note": "state uploaded once from pinned host memory inside "
                           "the timed region, particle state read back after every step"}
         return out, sim
+
+    def other_leg(name, steps=200, warmup=10):
+        """Step rate and fluid-kernel roofline of another workload (FP32)."""
+        ws = make_workloads(name, rank)
+        sim = lbm.from_workloads(ws)
+        sim.autotune(3)
+        sim.set_graphs(16)
+        st = sim.stream
+        sim.step(warmup)
+        sim.sync()
+        torch.cuda.synchronize()
+        barrier()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(st)
+        sim.step(steps)
+        e[1].record(st)
+        torch.cuda.synchronize()
+        sim.sync()
+        ms = max_over_ranks(e[0].elapsed_time(e[1]), world, "cuda")
+        for _ in range(3):
+            sim.fluid_step_only()
+        e[2].record(st)
+        for _ in range(100):
+            sim.fluid_step_only()
+        e[3].record(st)
+        torch.cuda.synchronize()
+        kms = e[2].elapsed_time(e[3]) / 100
+        nodes = sim.total_nodes
+        bpn = bytes_per_node(ws[0].D, "fp32")
+        peak, kind = measured_peak()
+        ach = nodes * bpn / (kms / 1e3) / 1e9
+        shape = sim.kernel_shape()
+        sim.close()
+        return {"value": world * nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+                "ms_per_step": ms / steps, "config": describe(name, ws, "fp32"),
+                "kernel_shape": {"vec": shape[0], "tile_rows": shape[1], "warps": shape[2]},
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "kernel_ms": kms, "algorithmic_bytes_per_node": bpn, "peak_kind": f"hbm_gbs of {kind}"}}
 
     storage = args.storage
     res, sim = leg(storage, args.steps, args.warmup, not args.no_e2e, True)
@@ -413,6 +460,8 @@ def main():
                                              "kernel_ms": r16["kernel_ms"],
                                              "traffic": traffic_per_launch("fp16", args.workload)},
                                 "speedup_vs_fp32": v16 / value}
+    if not args.no_other_workloads and args.workload == "many_disks":
+        line["other_workloads"] = {name: other_leg(name) for name in ("ensemble", "spheres3d")}
     if not args.no_adjoint and args.workload == "many_disks":
         adj = adjoint_leg(lbm, torch, rank, args.adjoint_steps)
         line["adjoint_forward_ratio"] = adj["ratio"]
