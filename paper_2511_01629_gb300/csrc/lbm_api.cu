@@ -36,7 +36,7 @@ bool tma_rows_ok(int rows);
 int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages);
 cudaError_t launch_fluid_tma(int Q, int fp16, const InstDesc* insts, const void* tmaps,
                              const uint16_t* tile_inst, int ntiles, int par, const Shape& sh,
-                             int commit, int grid, int* tile_ctr, int stages, cudaStream_t st);
+                             int commit, int grid, int* tile_ctr, int stages, int ninst, cudaStream_t st);
 cudaError_t launch_adj_fluid(int Q, int fp16, const InstDesc* insts, const AdjFluid* afs,
                              const uint16_t* tile_inst, int ntiles, int lam_mode, const Shape& sh,
                              cudaStream_t st);
@@ -489,7 +489,7 @@ int enqueue_fluid(lbm_ctx* ctx, int commit, cudaStream_t st) {
     if (sh.tma) {
         CK(launch_fluid_tma(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), ctx->d_tmaps.ptr,
                             P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, ctx->par, sh, commit,
-                            ctx->grid, P<int>(ctx->d_tile_ctr), sh.stages, st));
+                            ctx->grid, P<int>(ctx->d_tile_ctr), sh.stages, (int)ctx->inst.size(), st));
         return LBM_OK;
     }
     CK(launch_fluid(ctx->Q, ctx->fp16, P<InstDesc>(ctx->d_insts), P<uint16_t>(ctx->d_tile_inst),
@@ -1420,7 +1420,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
             if (sh.tma)
                 CK(launch_fluid_tma(ctx->Q, ctx->fp16, dk, P<CUtensorMap>(A.d_rtmaps) + (size_t)k * ni * 2,
                                     P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1, ctx->grid,
-                                    P<int>(ctx->d_tile_ctr), sh.stages, st));
+                                    P<int>(ctx->d_tile_ctr), sh.stages, ni, st));
             else
                 CK(launch_fluid(ctx->Q, ctx->fp16, dk, P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1,
                                 sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), st));

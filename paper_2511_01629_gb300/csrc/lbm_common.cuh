@@ -521,21 +521,13 @@ __device__ __forceinline__ void collide(float* f, const float* a, bool solid, co
     *p_out = p2.x;
 }
 
-// Exact fixed-point image round(u * 2^FXBITS) of a velocity component, with
-// integer operations only (the value is clamped to |u| < 1/2; a larger or
-// non-finite velocity is reported as divergence by the caller).
+// Fixed-point image round(u * 2^FXBITS) of a velocity component, rounded to
+// the nearest integer (ties to even): the scaling by a power of two is exact,
+// so the conversion is the only rounding.  The value is clamped to |u| < 1/2;
+// a larger or non-finite velocity is reported as divergence by the caller.
 __device__ __forceinline__ long long to_fx(float u) {
     u = fminf(fmaxf(u, -0.49999997f), 0.49999997f);
-    const int b = __float_as_int(u);
-    const int e = (b >> 23) & 0xff;
-    if (e == 0) return 0;
-    const long long m = (long long)((b & 0x7fffff) | 0x800000);
-    const int sh = e - 150 + FXBITS;  // |u| = m * 2^(e - 150)
-    long long v;
-    if (sh >= 0) v = m << sh;
-    else if (sh > -25) v = (m + (1LL << (-sh - 1))) >> (-sh);
-    else v = 0;
-    return b < 0 ? -v : v;
+    return __float2ll_rn(u * 1099511627776.0f);  // u * 2^40 is exact; round to nearest even
 }
 
 // Exact warp sum of a 64-bit integer of magnitude below 2^51: three 21-bit

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                                                    const CUtensorMap* __restrict__ tmaps,
                                                    const uint16_t* __restrict__ tile_inst, int ntiles,
                                                    int par, Shape sh, int commit, int* tile_ctr,
-                                                   int stages) {
+                                                   int stages, int ninst) {
     using L = Lat<Q>;
     constexpr int D = L::D;
     constexpr int QS = Q - 1;
@@ -174,6 +174,10 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         // atomic's latency hides behind the current tile's staging
         int t_next = 0;
         if (lane == 0) t_next = atomicAdd(&tile_ctr[0], 1);
+        // instance of a tile without a memory round trip: a vote over the
+        // instances' first tiles held in the lanes (the table for > 32 instances)
+        int tile0_l = 0x7fffffff;
+        if (ninst <= 32 && lane < ninst) tile0_l = insts[lane].tile0;
         for (int it = 0;; ++it) {
             const int s = it % stages;
             const uint32_t ph = (uint32_t)(it / stages) & 1u;
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 }
                 break;
             }
-            const int ii = tile_inst[t];
+            const int ii = ninst <= 32 ? __popc(__ballot_sync(0xffffffffu, t >= tile0_l)) - 1 : tile_inst[t];
             const InstDesc& in = insts[ii];
             const int local = t - in.tile0;
             const int ntx = in.ntile[0], nty = in.ntile[1];
@@ -410,11 +414,11 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
 template <int Q, class S, int TW, int ROWS>
 static cudaError_t launch_tma_t(const InstDesc* insts, const void* tmaps, const uint16_t* tile_inst,
                                 int ntiles, int par, const Shape& sh, int commit, int grid,
-                                int* tile_ctr, int stages, cudaStream_t st) {
+                                int* tile_ctr, int stages, int ninst, cudaStream_t st) {
     const TmaLayout LY = tma_layout(Q, (int)sizeof(S), TW, ROWS, stages);
     k_fluid_tma<Q, S, TW, ROWS><<<grid, 32 * (sh.warps + 1), LY.bytes, st>>>(
         insts, static_cast<const CUtensorMap*>(tmaps), tile_inst, ntiles, par, sh, commit, tile_ctr,
-        stages);
+        stages, ninst);
     return cudaGetLastError();
 }
 
@@ -456,9 +460,10 @@ int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages) {
 
 cudaError_t launch_fluid_tma(int Q, int fp16, const InstDesc* insts, const void* tmaps,
                              const uint16_t* tile_inst, int ntiles, int par, const Shape& sh,
-                             int commit, int grid, int* tile_ctr, int stages, cudaStream_t st) {
-#define LBM_LAUNCH(QQ, SS, TT, RR) \
-    launch_tma_t<QQ, SS, TT, RR>(insts, tmaps, tile_inst, ntiles, par, sh, commit, grid, tile_ctr, stages, st)
+                             int commit, int grid, int* tile_ctr, int stages, int ninst, cudaStream_t st) {
+#define LBM_LAUNCH(QQ, SS, TT, RR)                                                                    \
+    launch_tma_t<QQ, SS, TT, RR>(insts, tmaps, tile_inst, ntiles, par, sh, commit, grid, tile_ctr, stages, \
+                                 ninst, st)
     LBM_TMA_DISPATCH(LBM_LAUNCH)
 #undef LBM_LAUNCH
     return cudaErrorInvalidValue;
