@@ -127,6 +127,61 @@ def test_moving_wall_couette():
 
 
 @gpu
+def test_spheres3d_full_size_2_steps():
+    """The D3Q19 workload at full size (256x256x512, 8 spheres R = 10, graph
+    replay, the autotuned shape the bench times) against the oracle."""
+    import oracle
+    from harness import oracle_config
+    w = W.spheres3d(seed=0)
+    sim = lbm.from_workloads([w])
+    sim.autotune(2)
+    sim.set_graphs(16)
+    sim.step(2)
+    sim.sync()
+    ref = oracle.Sim(oracle_config(w))
+    ref.add_particles(w.pos, w.radius, w.ratio)
+    ref.step(2)
+    cf = compare_fields(sim, ref)
+    cp = compare_particles(sim, ref)
+    sim.close()
+    ref.close()
+    assert cf["owner_equal"], cf
+    assert cf["du"] < 2e-6, cf
+    assert cp["count_equal"], cp
+    assert cp["dU"] < 2e-6 * cp["Uscale"], cp
+
+
+@gpu
+def test_ensemble_full_size_2_steps():
+    """The 64-instance batched ensemble in one launch per step (the bench's
+    configuration): its smallest and largest instances against oracle runs of
+    those instances alone."""
+    import oracle
+    from harness import oracle_config
+    ws = W.ensemble(seed=0)
+    sim = lbm.from_workloads(ws)
+    sim.autotune(2)
+    sim.set_graphs(16)
+    sim.step(2)
+    sim.sync()
+    order = np.argsort([w.nodes for w in ws])
+    for i in (int(order[0]), int(order[-1])):
+        w = ws[i]
+        ref = oracle.Sim(oracle_config(w))
+        if w.num_particles:
+            ref.add_particles(w.pos, w.radius, w.ratio)
+        ref.step(2)
+        cf = compare_fields(sim, ref, i)
+        cp = compare_particles(sim, ref, i)
+        ref.close()
+        assert cf["owner_equal"], (i, cf)
+        assert cf["du"] < 2e-6, (i, cf)
+        assert cp["count_equal"], (i, cp)
+        assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-30), (i, cp)
+    sim.close()
+
+
+@gpu
 def test_many_disks_full_size_20_steps():
     """The benched workload at full size (1024x4096, 500 disks, graph replay, the
     autotuned kernel shape) against the oracle for 20 steps."""
