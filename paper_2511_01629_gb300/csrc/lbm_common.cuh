@@ -624,42 +624,82 @@ __device__ __forceinline__ double rcp64(double x) {
 // Moments about the integer reference floor(X) are shifted to the centre:
 //   sum r x u = sum d x u - phi x sum u,
 //   sum r r^T = sum d d^T - phi sum d^T - sum d phi^T + n phi phi^T.
+//
+// An FP64 instruction takes the FP64 pipe of its SM sub-partition for ~64
+// cycles whatever the number of active lanes, so the work is spread over
+// lanes by component: the translation (U^n, Ubar, predicted position) runs
+// one lane per component d, and the rotation (W^n) one lane per component on
+// another warp, concurrently.  Each lane evaluates the same expressions, in
+// the same order, as a serial loop over the components would.
+
+// Translational part, component d (0..2) of particle p.
 template <int D>
-__device__ void finalize_particle(const InstDesc& in, int p, const long long* v) {
+__device__ void finalize_translation(const InstDesc& in, int p, const long long* v, int d) {
     const PRec& pr = in.prec[p];
     // every operand is loaded before the first store, so the loads overlap
-    double X[3] = {0, 0, 0}, Uold[3] = {0, 0, 0}, phi[3] = {0, 0, 0};
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        X[d] = pr.X[d];
-        phi[d] = X[d] - (double)pr.ref[d];
-        Uold[d] = in.U[3 * p + d];
-    }
+    const double X = d < D ? pr.X[d] : 0.0;
+    const double Uold = d < D ? in.U[3 * p + d] : 0.0;
     const float Rf = (float)in.pconst[PCONST_N * p + PC_R];
     const double h = in.hK;
     if (v[0] == 0) {  // no solid node: cannot happen inside the box for R >= 2
-        atomicOr(in.status, ST_PARTICLE);
-        for (int d = 0; d < 3; ++d) {
-            in.Un[3 * p + d] = in.U[3 * p + d];
-            in.Wn[3 * p + d] = 0.0;
+        if (d == 0) {
+            atomicOr(in.status, ST_PARTICLE);
+            in.count[p] = 0;
         }
-        in.count[p] = 0;
+        in.Un[3 * p + d] = in.U[3 * p + d];
         return;
     }
     const double cnt = (double)v[0];
     const double inv = rcp64(cnt);
-    double Su[3] = {0, 0, 0}, Uo[3] = {0, 0, 0}, Wo[3] = {0, 0, 0};
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        Su[d] = (double)v[10 + d] * FX_SCALE;
-        Uo[d] = Su[d] * inv;
+    double Uo = 0.0, ub = 0.0;
+    float Xs = 0.f;
+    bool fast = false;
+    if (d < D) {
+        const double Su = (double)v[10 + d] * FX_SCALE;
+        Uo = Su * inv;
+        ub = 0.5 * (Uo + Uold);
+        fast = !(fabs(ub) < 0.5);
+        Xs = (float)(X + h * ub);
     }
+    in.Un[3 * p + d] = Uo;
+    in.Ubar[3 * p + d] = ub;
+    in.Xk[3 * p + d] = X;  // sub-step buffer 0 = X^n
+    in.Xf[4 * p + d] = (float)X;
+    in.Xsf[4 * p + d] = Xs;
+    if (d == 0) {
+        in.Xf[4 * p + 3] = Rf;
+        in.Xsf[4 * p + 3] = Rf;
+        in.count[p] = (int)v[0];
+        in.invc[p] = inv;
+    }
+    if (fast) atomicOr(in.status, ST_DISPLACEMENT);
+}
+
+// Rotational part, component c (0..2) of W^n of particle p, and the sums the
+// adjoint records (component 0's lane).
+template <int D>
+__device__ void finalize_rotation(const InstDesc& in, int p, const long long* v, int c) {
+    const PRec& pr = in.prec[p];
+    double phi[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) phi[d] = pr.X[d] - (double)pr.ref[d];
+    if (v[0] == 0) {
+        in.Wn[3 * p + c] = 0.0;
+        return;
+    }
+    const double cnt = (double)v[0];
+    double Su[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) Su[d] = (double)v[10 + d] * FX_SCALE;
+    double Wo = 0.0;
     if (D == 2) {
-        // w_z = sum (r x u)_z / sum |r|^2
-        const double Lz = (double)v[15] * FX_SCALE - (phi[0] * Su[1] - phi[1] * Su[0]);
-        const double Izz = (double)(v[4] + v[5]) - 2.0 * (phi[0] * (double)v[1] + phi[1] * (double)v[2]) +
-                           cnt * (phi[0] * phi[0] + phi[1] * phi[1]);
-        Wo[2] = Lz * rcp64(Izz);
+        if (c == 2) {
+            // w_z = sum (r x u)_z / sum |r|^2
+            const double Lz = (double)v[15] * FX_SCALE - (phi[0] * Su[1] - phi[1] * Su[0]);
+            const double Izz = (double)(v[4] + v[5]) - 2.0 * (phi[0] * (double)v[1] + phi[1] * (double)v[2]) +
+                               cnt * (phi[0] * phi[0] + phi[1] * phi[1]);
+            Wo = Lz * rcp64(Izz);
+        }
     } else {
         const double Sd[3] = {(double)v[1], (double)v[2], (double)v[3]};
         double Sl[3];
@@ -683,17 +723,17 @@ __device__ void finalize_particle(const InstDesc& in, int p, const long long* v)
                            I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
                            I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
         const double idet = rcp64(det);
-        for (int col = 0; col < 3; ++col) {
-            double M[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int q = 0; q < 3; ++q) M[r][q] = (q == col) ? Lv[r] : I[r][q];
-            const double dc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
-                              M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                              M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-            Wo[col] = dc * idet;
-        }
+        // Cramer's rule: column c of I replaced by L
+        double M[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) M[r][q] = (q == c) ? Lv[r] : I[r][q];
+        const double dc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                          M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                          M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        Wo = dc * idet;
     }
-    if (in.adj_geo) {  // adjoint recording: the sums about X^n that the projection used
+    in.Wn[3 * p + c] = Wo;
+    if (in.adj_geo && c == 0) {  // adjoint recording: the sums about X^n that the projection used
         double* g = in.adj_geo + (long long)NPV * p;
         const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
         g[0] = cnt;
@@ -708,26 +748,6 @@ __device__ void finalize_particle(const InstDesc& in, int p, const long long* v)
         g[14] = (double)v[14] * FX_SCALE - (phi[2] * Su[0] - phi[0] * Su[2]);
         g[15] = (double)v[15] * FX_SCALE - (phi[0] * Su[1] - phi[1] * Su[0]);
     }
-    bool fast = false;
-    float Xs[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        in.Un[3 * p + d] = Uo[d];
-        in.Wn[3 * p + d] = Wo[d];
-        double ub = 0.0;
-        if (d < D) {
-            ub = 0.5 * (Uo[d] + Uold[d]);
-            fast |= !(fabs(ub) < 0.5);
-            Xs[d] = (float)(X[d] + h * ub);
-        }
-        in.Ubar[3 * p + d] = ub;
-        in.Xk[3 * p + d] = X[d];  // sub-step buffer 0 = X^n
-    }
-    reinterpret_cast<float4*>(in.Xf)[p] = make_float4((float)X[0], (float)X[1], (float)X[2], Rf);
-    reinterpret_cast<float4*>(in.Xsf)[p] = make_float4(Xs[0], Xs[1], Xs[2], Rf);
-    in.count[p] = (int)v[0];
-    in.invc[p] = inv;
-    if (fast) atomicOr(in.status, ST_DISPLACEMENT);
 }
 
 template <int Q, class S>

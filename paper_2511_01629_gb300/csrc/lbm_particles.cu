@@ -90,25 +90,24 @@ __device__ void gather_pairs(const double* f1, const double* f2, double* F1, dou
     }
 }
 
-// Wall part of Eq. 21 (mirror images across the planes -1/2 and n - 1/2).
-__device__ void wall_force(const InstDesc& in, const double* Xi, double* F, double cw, double inv_delta,
-                           double Ri) {
+// Wall part of Eq. 21 (mirror images across the planes -1/2 and n - 1/2),
+// component d of the force on a particle at coordinate Xi along axis d.
+__device__ void wall_force_d(const InstDesc& in, int d, double Xi, double& F, double cw, double inv_delta,
+                             double Ri) {
     if (cw == 0.0) return;  // cw = C / eps_w of the particle
     const float reach = 0.5f * (2.0f * (float)Ri + (float)in.delta) + 0.01f;
-    for (int d = 0; d < 3; ++d) {
-        if (in.periodic[d] || in.n[d] <= 1) continue;
-        const float xf = (float)Xi[d];  // skip walls farther than (2R + delta)/2
-        if (xf + 0.5f > reach && (float)in.n[d] - 0.5f - xf > reach) continue;
-        const double walls[2] = {-0.5, in.n[d] - 0.5};
-        for (int face = 0; face < 2; ++face) {
-            const double Xim = 2.0 * walls[face] - Xi[d];
-            const double diff = Xi[d] - Xim;
-            const double dprime = fabs(diff);
-            const double range = 2.0 * Ri + in.delta;
-            if (dprime <= range) {
-                const double sc = (range - dprime) * inv_delta;
-                F[d] += cw * diff * sc * sc;
-            }
+    if (in.periodic[d] || in.n[d] <= 1) return;
+    const float xf = (float)Xi;  // skip walls farther than (2R + delta)/2
+    if (xf + 0.5f > reach && (float)in.n[d] - 0.5f - xf > reach) return;
+    const double walls[2] = {-0.5, in.n[d] - 0.5};
+    for (int face = 0; face < 2; ++face) {
+        const double Xim = 2.0 * walls[face] - Xi;
+        const double diff = Xi - Xim;
+        const double dprime = fabs(diff);
+        const double range = 2.0 * Ri + in.delta;
+        if (dprime <= range) {
+            const double sc = (range - dprime) * inv_delta;
+            F += cw * diff * sc * sc;
         }
     }
 }
@@ -165,37 +164,58 @@ __device__ __forceinline__ int axis_tile(const AxisTiles& t, int i) {
     return i < t.na ? t.a0 + i : t.b0 + (i - t.na);
 }
 
-// Record of particle p at its current X and A for the next fluid step, and
-// the tiles of its bounding box (slots k enumerate them x-fastest; no tile is
-// listed twice).  One thread.
-// Record of particle p from its new state (X, A) and constants (R, 1 - rho_f/rho_s).
-__device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at,
-                                 const double* Xp, const double* Ap, double R, float gfac) {
+// Component d of a particle's record for the next fluid step: the reference
+// node floor(X), the offset from it, the acceleration term of the penalty
+// force, and the tiles of the bounding box [X - R - 1, X + R + 1] along d (its
+// one-node margin covers the float rounding).
+struct RecComp {
+    int ref;
+    float frac, a;
+    AxisTiles t;
+};
+
+__device__ __forceinline__ RecComp record_component(const InstDesc& in, int d, int D, const Shape& sh, double X,
+                                                    double A, float Rf, float gfac) {
+    const int T = d == 0 ? sh.tw : (d == 1 ? sh.ty : sh.tz);
+    RecComp r;
+    r.ref = d < D ? __double2int_rd(X) : 0;
+    r.frac = (float)(X - (double)r.ref);
+    r.a = fmaf(gfac, in.ggrav[d], (float)A);
+    r.t = d >= D ? AxisTiles{0, 1, 0, 0}
+                 : axis_tiles_f((float)r.ref + r.frac, Rf, in.n[d], T, in.ntile[d], in.periodic[d]);
+    return r;
+}
+
+// The radius fields and tile count of a record (nt tiles of the bounding box).
+__device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, double R, int nt) {
     const float Rf = (float)R;
-    const int T[3] = {sh.tw, sh.ty, sh.tz};
-    int cnt[3];
-    PRec pr;
-    for (int d = 0; d < 3; ++d) {
-        const double X = Xp[d];
-        pr.X[d] = X;
-        const int ref = d < D ? __double2int_rd(X) : 0;
-        pr.ref[d] = ref;
-        pr.frac[d] = (float)(X - (double)ref);
-        pr.a[d] = fmaf(gfac, in.ggrav[d], (float)Ap[d]);
-        // box [X - R - 1, X + R + 1]: its one-node margin covers the float rounding
-        at[d] = d >= D ? AxisTiles{0, 1, 0, 0}
-                       : axis_tiles_f((float)ref + pr.frac[d], Rf, in.n[d], T[d], in.ntile[d], in.periodic[d]);
-        cnt[d] = at[d].na + at[d].nb;
-    }
-    const int nt = cnt[0] * cnt[1] * cnt[2];
     pr.R2 = R * R;
     const float R2f = Rf * Rf;
     pr.R2lo = R2f * (1.0f - 2e-5f) - 2e-4f;
     pr.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
     pr.ntiles = nt;
     pr.pad = 0;
-    in.prec_out[p] = pr;
     if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
+}
+
+// Record of particle p from its state (X, A) and constants (R, 1 - rho_f/rho_s),
+// with the tiles of its bounding box (slots k enumerate them x-fastest; no tile
+// is listed twice).  One thread.
+__device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at,
+                                 const double* Xp, const double* Ap, double R, float gfac) {
+    PRec pr;
+    int nt = 1;
+    for (int d = 0; d < 3; ++d) {
+        const RecComp r = record_component(in, d, D, sh, Xp[d], Ap[d], (float)R, gfac);
+        pr.X[d] = Xp[d];
+        pr.ref[d] = r.ref;
+        pr.frac[d] = r.frac;
+        pr.a[d] = r.a;
+        at[d] = r.t;
+        nt *= r.t.na + r.t.nb;
+    }
+    record_radius(in, pr, R, nt);
+    in.prec_out[p] = pr;
 }
 
 __device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at) {
@@ -225,85 +245,92 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
     }
 }
 
-// Algorithm 1 for particle i (one thread): wall forces, the corrected
-// position, and on the last sub-step A^{n+1}, theta^{n+1}, U^{n-1} <- U^n
-// and the record for the next step.
-__device__ void update_particle(const InstDesc& in, int i, const double* F1in, const double* F2in,
-                                int src, double h, int last, int D, const Shape& sh, AxisTiles* at) {
-    const int dst = src ^ 1;
-    const double* Xs = in.Xk + (long long)src * in.np * 3;
-    // every operand up front, in one batch of loads: the FP64 chain below then
-    // runs without further round trips to memory
-    double X0[3], Ub[3], Xold[3], F1[3], F2[3], Wn[3], Un[3], Wo[3], Th[3];
-    for (int d = 0; d < 3; ++d) {
-        X0[d] = Xs[3 * i + d];
-        Ub[d] = in.Ubar[3 * i + d];
-        Xold[d] = in.X[3 * i + d];
-        F1[d] = F1in[d];
-        F2[d] = F2in[d];
-        Wn[d] = in.Wn[3 * i + d];
-        Un[d] = in.Un[3 * i + d];
-        Wo[d] = in.W[3 * i + d];
-        Th[d] = in.theta[3 * i + d];
+// Algorithm 1 for particle i, component d (one lane per component; the lanes
+// of particle slot sl are sl + PB * d, and lanes with valid = false take part
+// in the shuffles only): wall forces, the corrected position, and on the last
+// sub-step A^{n+1}, theta^{n+1}, U^{n-1} <- U^n and the record for the next
+// step.  Each lane evaluates the expressions of a serial loop over d.
+__device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid, const double* F1in,
+                            const double* F2in, int src, double h, int last, int D, const Shape& sh,
+                            AxisTiles* at) {
+    if (!valid) {  // in-range operands for the shuffle-only lanes; nothing is stored
+        i = 0;
+        d = 0;
     }
+    const int dst = src ^ 1;
+    const long long j = 3LL * i + d;
+    // every operand up front, in one batch of loads
+    const double X0 = in.Xk[(long long)src * in.np * 3 + j];
+    const double Ub = in.Ubar[j], Xold = in.X[j], Wn = in.Wn[j], Un = in.Un[j], Wo = in.W[j], Th = in.theta[j];
+    double F1 = F1in[d], F2 = F2in[d];
     const double* pc = in.pconst + PCONST_N * i;
     const double invrhos = pc[PC_INVRHOS], cw = pc[PC_CWALL], idl = pc[PC_INVDELTA], Ri = pc[PC_R];
     const double gfac = pc[PC_GFAC];
     const double invc = in.invc[i];
     const int cnt = in.count[i];
     const double invM = invrhos * invc;  // 1 / (rho_s n)
-    double Xst[3];
-    for (int d = 0; d < 3; ++d) Xst[d] = fma(h, Ub[d], X0[d]);
-    wall_force(in, X0, F1, cw, idl, Ri);
-    wall_force(in, Xst, F2, cw, idl, Ri);
+    const double Xst = fma(h, Ub, X0);
+    wall_force_d(in, d, X0, F1, cw, idl, Ri);
+    wall_force_d(in, d, Xst, F2, cw, idl, Ri);
     const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
-    double Xn[3];
-    for (int d = 0; d < 3; ++d) Xn[d] = Xst[d] + c * (F1[d] + F2[d]);
+    const double Xn = Xst + c * (F1 + F2);
+    const float Rf = (float)Ri;
     if (!last) {
-        double* Xd = in.Xk + (long long)dst * in.np * 3;
-        for (int d = 0; d < 3; ++d) Xd[3 * i + d] = Xn[d];
-        const float Rf = (float)Ri;
-        reinterpret_cast<float4*>(in.Xf)[(long long)dst * in.np + i] =
-            make_float4((float)Xn[0], (float)Xn[1], (float)Xn[2], Rf);
-        reinterpret_cast<float4*>(in.Xsf)[(long long)dst * in.np + i] =
-            make_float4((float)fma(h, Ub[0], Xn[0]), (float)fma(h, Ub[1], Xn[1]), (float)fma(h, Ub[2], Xn[2]), Rf);
+        if (valid) {
+            in.Xk[(long long)dst * in.np * 3 + j] = Xn;
+            float* xf = in.Xf + ((long long)dst * in.np + i) * 4;
+            float* xsf = in.Xsf + ((long long)dst * in.np + i) * 4;
+            xf[d] = (float)Xn;
+            xsf[d] = (float)fma(h, Ub, Xn);
+            if (d == 0) {
+                xf[3] = Rf;
+                xsf[3] = Rf;
+            }
+        }
         return;
     }
     bool left = false;
-    double An[3], Xw[3], Tn[3];
-    for (int d = 0; d < 3; ++d) {
-        An[d] = 2.0 * (Xn[d] - Xold[d] - Ub[d]);
-        double xn = Xn[d];
-        if (d < D) {
-            if (in.periodic[d]) {
-                if (xn >= in.n[d]) xn -= in.n[d];
-                else if (xn < 0.0) xn += in.n[d];
-            } else if (xn < -0.5 || xn > in.n[d] - 0.5) {
-                left = true;
-            }
+    const double An = 2.0 * (Xn - Xold - Ub);
+    double xn = Xn;
+    if (d < D) {
+        if (in.periodic[d]) {
+            if (xn >= in.n[d]) xn -= in.n[d];
+            else if (xn < 0.0) xn += in.n[d];
+        } else if (xn < -0.5 || xn > in.n[d] - 0.5) {
+            left = true;
         }
-        Xw[d] = xn;
-        Tn[d] = Th[d] + 0.5 * (Wn[d] + Wo[d]);
-        const int j = 3 * i + d;
-        in.A[j] = An[d];
+    }
+    const double Tn = Th + 0.5 * (Wn + Wo);
+    if (valid) {
+        in.A[j] = An;
         in.X[j] = xn;
-        in.theta[j] = Tn[d];
-        in.U[j] = Un[d];
-        in.W[j] = Wn[d];
-    }
-    if (left) atomicOr(in.status, ST_PARTICLE);
-    if (in.rec_state) {  // adjoint recording: the state this step hands to the next
-        double* r = in.rec_state + 16LL * i;
-        for (int d = 0; d < 3; ++d) {
-            r[d] = Xw[d];
-            r[3 + d] = Un[d];
-            r[6 + d] = Wn[d];
-            r[9 + d] = Tn[d];
-            r[12 + d] = An[d];
+        in.theta[j] = Tn;
+        in.U[j] = Un;
+        in.W[j] = Wn;
+        if (left) atomicOr(in.status, ST_PARTICLE);
+        if (in.rec_state) {  // adjoint recording: the state this step hands to the next
+            double* r = in.rec_state + 16LL * i;
+            r[d] = xn;
+            r[3 + d] = Un;
+            r[6 + d] = Wn;
+            r[9 + d] = Tn;
+            r[12 + d] = An;
+            if (d == 0) r[15] = (double)cnt;
         }
-        r[15] = (double)cnt;
     }
-    make_record_from(in, i, D, sh, at, Xw, An, Ri, (float)gfac);
+    const RecComp r = record_component(in, d, D, sh, xn, An, Rf, (float)gfac);
+    const int ct = r.t.na + r.t.nb;
+    const int nt = __shfl_sync(0xffffffffu, ct, sl) * __shfl_sync(0xffffffffu, ct, sl + PB) *
+                   __shfl_sync(0xffffffffu, ct, sl + 2 * PB);
+    if (valid) {
+        PRec& pr = in.prec_out[i];
+        pr.X[d] = xn;
+        pr.ref[d] = r.ref;
+        pr.frac[d] = r.frac;
+        pr.a[d] = r.a;
+        at[d] = r.t;
+        if (d == 0) record_radius(in, pr, Ri, nt);
+    }
 }
 
 // ------------------------------------------------------------- the kernel --
@@ -377,9 +404,17 @@ __device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntot
         }
     }
     __syncthreads();
-    if (warp == 0 && lane < PB && gp0 + lane < ntotal && refs[gp0 + lane].inst >= 0) {
-        if (D == 2) finalize_particle<2>(in, refs[gp0 + lane].p, tot[lane]);
-        else finalize_particle<3>(in, refs[gp0 + lane].p, tot[lane]);
+    // one lane per (particle, component): translation on warp 0, rotation on warp 1
+    const int sl = lane & (PB - 1), c = lane / PB;
+    if (warp < 2 && c < 3 && gp0 + sl < ntotal && refs[gp0 + sl].inst >= 0) {
+        const int p = refs[gp0 + sl].p;
+        if (warp == 0) {
+            if (D == 2) finalize_translation<2>(in, p, tot[sl], c);
+            else finalize_translation<3>(in, p, tot[sl], c);
+        } else {
+            if (D == 2) finalize_rotation<2>(in, p, tot[sl], c);
+            else finalize_rotation<3>(in, p, tot[sl], c);
+        }
     }
 }
 
@@ -433,8 +468,12 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
             }
     }
     __syncthreads();
-    if (warp == 0 && lane < PB && gp0 + lane < ntotal && refs[gp0 + lane].inst >= 0)
-        update_particle(in, refs[gp0 + lane].p, sF[lane], sF[lane] + 3, src, h, last, D, sh, sAT[lane]);
+    if (warp == 0) {  // one lane per (particle, component)
+        const int sl = lane & (PB - 1), d = lane / PB;
+        const bool valid = d < 3 && gp0 + sl < ntotal && refs[gp0 + sl].inst >= 0;
+        update_lane(in, valid ? refs[gp0 + sl].p : 0, d, sl, valid, sF[sl], sF[sl] + 3, src, h, last, D, sh,
+                    sAT[sl]);
+    }
 }
 
 // Particle part of one time step for the block's 8 particles (one instance),
