@@ -20,7 +20,11 @@ Workloads (lattice units, dx = dt = rho_f = 1; Sec. 3 sets alpha = 1/tau):
     1..50 disks each drawn like ``many_disks``;
   * ``spheres3d``  D3Q19 256x256x512 closed box, 8 spheres R = 10, ratio 1.5,
     gravity 2e-6 in -z, seeded in the top half;
-  * ``adjoint_disk`` the ``single_disk`` physics used for gradients.
+  * ``adjoint_disk`` the ``single_disk`` physics used for gradients;
+  * ``disk_column``  96x240 closed box, gravity 4e-5, disks R = 6 stacked
+    with gaps of 0.4 (inside the collision range delta = 1) and one disk
+    within range of the wall x = -1/2, so that the pair and wall forces of
+    Eq. 21 act from the first step.
 """
 from __future__ import annotations
 
@@ -158,6 +162,21 @@ def spheres3d(seed: int = 0, nx: int = 256, ny: int = 256, nz: int = 512, count:
     pos, rad, rat = _sample_disks(rng, count, (nx, ny, nz), 3, radius, radius, 1.5, 1.5, 1.0, 2)
     return Workload("spheres3d", 3, (nx, ny, nz), (0, 0, 0), tau=1.0, alpha=1.0,
                     g_grav=(0.0, 0.0, -2e-6), pos=pos, radius=rad, ratio=rat, steps=steps)
+
+
+def disk_column(seed: int = 0, nx: int = 96, ny: int = 240, count: int = 6, radius: float = 6.0,
+                gap: float = 0.4, K: int = 1) -> Workload:
+    rng = SplitMix64(seed)
+    pos, rad, rat = [], [], []
+    for k in range(count):
+        pos.append([nx / 2.0 + rng.uniform(-0.5, 0.5), 0.25 * ny + k * (2.0 * radius + gap)])
+        rad.append(radius)
+        rat.append(rng.uniform(1.2, 1.9))
+    pos.append([-0.5 + radius + 0.3, 0.5 * ny])  # 0.3 inside the wall's range R + delta/2
+    rad.append(radius)
+    rat.append(1.5)
+    return Workload("disk_column", 2, (nx, ny, 1), (0, 0, 1), tau=1.0, alpha=1.0,
+                    g_grav=(0.0, -4e-5, 0.0), K=K, pos=pos, radius=rad, ratio=rat, steps=150)
 
 
 def adjoint_disk(seed: int = 0, nx: int = 400, ny: int = 1600, steps: int = 5000) -> Workload:

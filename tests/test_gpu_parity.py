@@ -182,6 +182,26 @@ def test_ensemble_full_size_2_steps():
 
 
 @gpu
+@pytest.mark.parametrize("K", [1, 2])
+def test_colliding_disks_match_oracle(K):
+    """Disks in contact (pair forces of Eq. 21 from the first step) and a disk
+    within wall range, with K = 1 and 2 sub-steps of Algorithm 1 (the grid
+    barrier between sub-steps), against the oracle for 150 steps."""
+    w = W.disk_column(seed=7, K=K)
+    sim, ref = make_pair(w)
+    sim.step(w.steps)
+    ref.step(w.steps)
+    sim.sync()
+    cf = compare_fields(sim, ref)
+    cp = compare_particles(sim, ref)
+    assert cf["owner_equal"], cf
+    assert cf["du"] < 5e-6, cf
+    assert cp["count_equal"], cp
+    assert cp["dU"] < 5e-6 * cp["Uscale"], cp
+    assert cp["dX"] < 1e-6, cp
+
+
+@gpu
 def test_many_disks_full_size_20_steps():
     """The benched workload at full size (1024x4096, 500 disks, graph replay, the
     autotuned kernel shape) against the oracle for 20 steps."""

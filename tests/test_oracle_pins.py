@@ -233,6 +233,24 @@ def test_collision_forces_by_hand(oracle):
     assert np.all(oracle.collision_forces(cfg0, [[30.0, 3.5]], [4.0], [1.5]) == 0)
 
 
+def test_disk_column_workload_is_in_contact(oracle):
+    """The contact workload of the GPU parity test engages Eq. 21 from the
+    first step: every column disk feels a pair force (the bottom one is pushed
+    down by its only neighbour, the top one up), and the disk beside the wall
+    x = -1/2 is pushed in +x."""
+    from paper_2511_01629_gb300 import workloads as W
+    w = W.disk_column(seed=7)
+    cfg = oracle.make_config(D=2, n=w.n, periodic=w.periodic, g_grav=w.g_grav, delta=w.delta,
+                             eps_p=w.eps_p, eps_w=w.eps_w)
+    F = oracle.collision_forces(cfg, w.pos, w.radius, w.ratio)
+    col = len(w.radius) - 1
+    assert np.all(np.abs(F[:col, 1]) > 0)
+    assert F[0, 1] < 0 and F[col - 1, 1] > 0  # the ends are pushed outwards
+    assert F[col, 0] > 0 and F[col, 1] == 0    # wall disk: +x only
+    far = [[p[0], p[1] + 40.0 * k] for k, p in enumerate(w.pos[:2])]
+    assert np.all(oracle.collision_forces(cfg, far, w.radius[:2], w.ratio[:2]) == 0)
+
+
 # -------------------------------------------------------------- dynamics ---
 
 def _uniform_state(oracle, D, n, U0):
