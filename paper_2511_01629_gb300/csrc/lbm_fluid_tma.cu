@@ -11,10 +11,13 @@
 // shared memory at x - c_x, collides them with packed FP32x2 arithmetic,
 // stores them to HBM with 8-byte coalesced stores, and reduces the
 // per-particle sums of Eq. 22.  Bytes in flight live in shared memory instead
-// of registers, which keeps HBM busy with few threads.  Rows whose source
-// lies beyond a face (walls or periodic wrap) and the nodes x = 0, nx - 1 read
-// those populations from HBM directly (bounce-back, wrap), as the
-// register-path kernel does.
+// of registers, which keeps HBM busy with few threads.  The populations the
+// x-edge node of a tile (x = 0 or nx - 1) pulls across its face (bounce-back
+// or periodic wrap) are gathered from HBM by the producer's lanes while the
+// copies are in flight, into a small per-stage array, so that the edge rows
+// stay on the shared-memory path; rows whose source lies beyond a y or z face
+// gather those populations from HBM directly, as the register-path kernel
+// does.
 //
 // Every mbarrier wait is bounded in time; on expiry the kernel records a
 // timeout in the status word, waits (bounded) for the copies it issued and
@@ -105,6 +108,9 @@ struct StageHdr {
     long long* partial;
     const PRec* prec;
     int* status;
+    int ex;   // x of the tile's edge node whose face values are staged, -1 none,
+              //   -2 both edges in one tile (those take the direct gathers)
+    int ecx;  // c_x of the staged populations: +1 at x = 0, -1 at x = nx - 1
 };
 
 }  // namespace
@@ -115,8 +121,12 @@ struct TmaLayout {
     int slab;        // bytes of one population box, rounded to 128
     int stage;       // bytes of all populations of one stage
     int pops_bytes;  // stages * stage
-    int hdr_off, cand_off, bar_off, bytes;
+    int hdr_off, cand_off, edge_off, bar_off, bytes;
 };
+
+// Populations with c_x = +1 (equally, -1): the ones an x-edge node pulls
+// across its face.
+__host__ __device__ constexpr int edge_pops(int Q) { return Q == 9 ? 3 : 5; }
 
 __host__ __device__ inline TmaLayout tma_layout(int Q, int ssize, int tw, int rows, int stages) {
     TmaLayout L;
@@ -127,7 +137,8 @@ __host__ __device__ inline TmaLayout tma_layout(int Q, int ssize, int tw, int ro
     L.pops_bytes = stages * L.stage;
     L.hdr_off = L.pops_bytes;
     L.cand_off = L.hdr_off + (int)sizeof(StageHdr) * stages;
-    L.bar_off = (L.cand_off + (int)sizeof(Cand) * LIST_CAP * stages + 15) & ~15;
+    L.edge_off = L.cand_off + (int)sizeof(Cand) * LIST_CAP * stages;
+    L.bar_off = (L.edge_off + (int)sizeof(float) * rows * edge_pops(Q) * stages + 15) & ~15;
     L.bytes = L.bar_off + 16 * stages + 128;  // + alignment slack of the base
     return L;
 }
@@ -153,6 +164,8 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
     const TmaLayout LY = tma_layout(Q, (int)sizeof(S), TW, rows, stages);
     StageHdr* hdr = reinterpret_cast<StageHdr*>(smem + LY.hdr_off);
     Cand* cands = reinterpret_cast<Cand*>(smem + LY.cand_off);
+    float* edgev = reinterpret_cast<float*>(smem + LY.edge_off);  // [stages][rows][QE]
+    constexpr int QE = edge_pops(Q);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + LY.bar_off);
     uint64_t* empty = full + stages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -217,6 +230,24 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                         tma_load_4d(dst + (q - 1) * LY.slab, map, x0 - H, y0 - cy, z0 - cz, q - 1, &full[s]);
                 }
             }
+            // the x-edge node's populations from across its face, one lane per
+            // (row, population): independent loads, in the shadow of the copies
+            const bool eleft = x0 == 0, eright = x0 + TW >= in.n[0];
+            const int ex = eleft && eright ? -2 : eleft ? 0 : eright ? in.n[0] - 1 : -1;
+            const int ecx = eleft ? 1 : -1;
+            if (ex >= 0) {
+                float* ev = edgev + s * rows * QE;
+                for (int l = lane; l < rows * QE; l += 32) {
+                    const int r = l / QE, k = l % QE;
+                    const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
+                    int q = 1;  // the k-th population with c_x = ecx
+                    for (int m = 0, qq = 1; qq < Q; ++qq)
+                        if (L::c(qq, 0) == ecx && m++ == k) q = qq;
+                    ev[l] = (y < in.n[1] && z < in.n[2])
+                                ? pull_scalar<Q, S>(in, static_cast<const S*>(in.f[par]), q, ex, y, z)
+                                : 0.f;
+                }
+            }
             int ncand = 0;
             if (in.np > 0) {
                 ncand = min(in.list_cnt[par][local], LIST_CAP);
@@ -264,8 +295,10 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 h.status = in.status;
                 h.tile = t;
                 h.ncand = ncand;
+                h.ex = ex;
+                h.ecx = ecx;
             }
-            __syncwarp();  // the lanes' candidate records are visible to lane 0's arrive
+            __syncwarp();  // the lanes' candidate and edge records are visible to lane 0's arrive
             if (lane == 0) mbar_arrive(&full[s]);
             ++issued;
         }
@@ -309,6 +342,8 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
         const int x0 = h.x0, y0 = h.y0, z0 = h.z0;
         const S* stage = reinterpret_cast<const S*>(smem + s * LY.stage);
+        const int ex = h.ex, ecx = h.ecx;
+        const float* ev = edgev + s * rows * QE;
         bool bad = false;
         for (int r = cw; r < rows; r += nc) {
             const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
@@ -329,12 +364,28 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 const int x = x0 + lx;
                 const bool v0 = x < nx, v1 = x + 1 < nx;
                 float2 f[QS];
-                if (rowfast && __all_sync(0xffffffffu, x > 0 && x + 1 < nx - 1)) {
+                if (rowfast && (ex >= 0 || __all_sync(0xffffffffu, x > 0 && x + 1 < nx - 1))) {
 #pragma unroll
                     for (int q = 1; q < Q; ++q) {
                         const S* src = rowbase + (q - 1) * SLAB + lx - L::c(q, 0);
                         if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, h.sload);
                         else f[q - 1] = make_float2(to_float_scaled(src[0], h.sload), to_float_scaled(src[1], h.sload));
+                    }
+                    // the edge node's populations from across the face (the box
+                    // holds zero fill or a neighbour column there); nodes past
+                    // nx in a ragged tile are computed but never stored
+                    const int e = ex - x;
+                    if (ex >= 0 && (e == 0 || e == 1)) {
+                        int k = 0;
+#pragma unroll
+                        for (int q = 1; q < Q; ++q) {
+                            if (L::c(q, 0) != 1 && L::c(q, 0) != -1) continue;
+                            if (L::c(q, 0) != ecx) continue;
+                            const float vv = ev[r * QE + k];
+                            ++k;
+                            if (e == 0) f[q - 1].x = vv;
+                            else f[q - 1].y = vv;
+                        }
                     }
                 } else {
 #pragma unroll
