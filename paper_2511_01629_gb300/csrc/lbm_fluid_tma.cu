@@ -1,7 +1,8 @@
 // TMA-pipelined variant of the fused stream-collide-penalize kernel.
 //
 // Persistent blocks of one producer warp and NC consumer warps.  The producer
-// takes tiles from a work counter (claimed one tile ahead) and issues one
+// takes tiles from a work counter (claimed one tile ahead; successive claims
+// alternate between the two ends of the tile range) and issues one
 // cp.async.bulk.tensor box per stored population: the source rows
 // (y - c_y, z - c_z) of the tile, 32*k nodes wide plus a 16-byte halo on both
 // sides so that every box starts on a 16-byte boundary; while the copies are
@@ -198,8 +199,11 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 ok = false;
                 break;
             }
-            const int t = __shfl_sync(0xffffffffu, t_next, 0);
-            if (t >= ntiles) {
+            const int claim = __shfl_sync(0xffffffffu, t_next, 0);
+            // claims alternate between the two ends of the tile range, so the
+            // slower boundary rows of both y faces come first, not last
+            const int t = (claim & 1) ? ntiles - 1 - (claim >> 1) : (claim >> 1);
+            if (claim >= ntiles) {
                 if (lane == 0) {
                     hdr[s].tile = -1;
                     mbar_arrive(&full[s]);
