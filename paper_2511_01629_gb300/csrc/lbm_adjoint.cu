@@ -392,6 +392,16 @@ __global__ void k_adj_pull_out(const InstDesc* __restrict__ insts, int inst, con
 // --------------------------------------------------------- particle sweep --
 namespace {
 
+// Whether a particle at coordinate Y (radius R) along wall axis d can be within
+// the wall range R + delta/2 of either plane -1/2, n - 1/2: an FP32 test with
+// a 0.01 margin (the forward kernel's filter), so that particles far from the
+// walls skip the FP64 range tests, whose outcome it cannot change.
+__device__ __forceinline__ bool wall_near(const InstDesc& in, int d, double Y, double R) {
+    const float reach = 0.5f * (2.0f * (float)R + (float)in.delta) + 0.01f;
+    const float yf = (float)Y;
+    return !(yf + 0.5f > reach && (float)in.n[d] - 0.5f - yf > reach);
+}
+
 // Collision force on particle i per unit C (Eqs. 19-21 with C = 1): pairs
 // with the lattice's minimum image, and mirror images across wall planes.
 __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, double* G) {
@@ -416,7 +426,7 @@ __device__ void unit_force(const InstDesc& in, int D, const double* Y, int i, do
         for (int d = 0; d < 3; ++d) G[d] += dv[d] * s * s * in.inv_eps_p;
     }
     for (int d = 0; d < D; ++d) {
-        if (in.periodic[d]) continue;
+        if (in.periodic[d] || !wall_near(in, d, Y[3 * i + d], in.R[i])) continue;
         const double walls[2] = {-0.5, in.n[d] - 0.5};
         for (int face = 0; face < 2; ++face) {
             const double diff = 2.0 * (Y[3 * i + d] - walls[face]);
@@ -464,7 +474,7 @@ __device__ void force_jt(const InstDesc& in, int D, const double* Y, const doubl
     }
     const double kw = in.pconst[PCONST_N * m + PC_CWALL];  // C_m / eps_w
     for (int d = 0; d < D; ++d) {
-        if (in.periodic[d]) continue;
+        if (in.periodic[d] || !wall_near(in, d, Y[3 * m + d], in.R[m])) continue;
         const double walls[2] = {-0.5, in.n[d] - 0.5};
         for (int face = 0; face < 2; ++face) {
             const double diff = 2.0 * (Y[3 * m + d] - walls[face]);

@@ -1,14 +1,15 @@
-// Per-particle FP64 kernels of lbmpen: the predictor-corrector of
-// Algorithm 1 with the repulsive collision forces (Eqs. 19-21) and the
-// rebuild of each particle's record and tile-list entries for the next step.
-// (The rigid-body projection of Eq. 22 is finalised at the end of the fused
-// fluid kernel, see lbm_common.cuh.)
+// Per-particle FP64 kernels of lbmpen: the second pass of the rigid-body
+// projection (Eq. 22; the per-component finalisation is in lbm_common.cuh),
+// the predictor-corrector of Algorithm 1 with the repulsive collision forces
+// (Eqs. 19-21), and the rebuild of each particle's record and tile-list
+// entries for the next step.
 //
-// GB300 runs FP64 at a small fraction of its FP32 rate and an FP64
-// instruction costs the same for one lane as for 32, so the serial
-// per-particle arithmetic runs one particle per thread.  The O(N^2) pair
-// search uses a warp per particle and filters pairs in FP32 (positions staged
-// in shared memory) before the FP64 evaluation of the few pairs in range.
+// GB300 runs FP64 at a small fraction of its FP32 rate, and an FP64
+// instruction occupies a sub-partition's FP64 pipe for ~64 cycles whether one
+// lane or 32 are active, so the serial per-particle arithmetic runs one lane
+// per (particle, vector component).  The O(N^2) pair search uses a warp per
+// particle and filters pairs in FP32 (positions staged in shared memory)
+// before the FP64 evaluation of the few pairs in range.
 #include "lbm_common.cuh"
 
 namespace lbmpen {
