@@ -147,14 +147,15 @@ def fluid_src_sha():
     return hh.hexdigest()[:16]
 
 
-def traffic_per_launch(storage, workload):
-    """DRAM bytes per fluid-kernel launch from the committed ncu capture, or None
-    when the kernel source changed since the capture."""
+def traffic_per_launch(storage, workload, shape):
+    """DRAM bytes per fluid-kernel launch from the committed ncu capture of this
+    workload, storage and kernel shape, or None when there is none or the kernel
+    source changed since the capture."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
         h = fluid_src_sha()
-        key = f"{workload}/{storage}"
+        key = f"{workload}/{storage}/{shape[0]},{shape[1]},{shape[2]}"
         if rec.get("fluid_src_sha") != h or key not in rec.get("bytes_per_launch", {}):
             return None
         return float(rec["bytes_per_launch"][key])
@@ -273,7 +274,9 @@ def main():
                     choices=["many_disks", "ensemble", "spheres3d", "single_disk"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the fluid kernel shape of the timed legs (default: the library's "
+                         "default shape, the one the committed profiles capture)")
     ap.add_argument("--no-fp16-leg", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
@@ -308,7 +311,7 @@ def main():
         sim = lbm.from_workloads(ws, st)
         if args.shape:
             sim.set_kernel_shape(*[int(v) for v in args.shape.split(",")])
-        elif not args.no_autotune:
+        elif args.autotune:
             sim.autotune(3)
         sim.set_graphs(16)
         stream = sim.stream
@@ -426,7 +429,8 @@ def main():
     bpn = bytes_per_node(D, storage)
     kms = res["kernel_ms"]
     achieved = nodes * bpn / (kms / 1e3) / 1e9
-    traffic = traffic_per_launch(storage, args.workload)
+    # an autotuned shape may differ from the captured one in its stage count
+    traffic = None if args.autotune else traffic_per_launch(storage, args.workload, res["shape"])
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -458,7 +462,10 @@ def main():
                                 "roofline": {"achieved": a16, "peak": peak, "frac": a16 / peak,
                                              "algorithmic_bytes_per_node": b16,
                                              "kernel_ms": r16["kernel_ms"],
-                                             "traffic": traffic_per_launch("fp16", args.workload)},
+                                             "traffic": None if args.autotune else
+                                             traffic_per_launch("fp16", args.workload, r16["shape"])},
+                                "kernel_shape": {"vec": r16["shape"][0], "tile_rows": r16["shape"][1],
+                                                 "warps": r16["shape"][2]},
                                 "speedup_vs_fp32": v16 / value}
     if not args.no_other_workloads and args.workload == "many_disks":
         line["other_workloads"] = {name: other_leg(name) for name in ("ensemble", "spheres3d")}

@@ -201,18 +201,31 @@ def test_colliding_disks_match_oracle(K):
     assert cp["dX"] < 1e-6, cp
 
 
-@gpu
-def test_many_disks_full_size_20_steps():
-    """The benched workload at full size (1024x4096, 500 disks, graph replay, the
-    autotuned kernel shape) against the oracle for 20 steps."""
+@pytest.fixture(scope="module")
+def many_disks_oracle_20():
+    """The oracle after 20 steps of the benched workload (computed once)."""
     w = W.many_disks(seed=0)
-    sim, ref = make_pair(w, graphs=16)
-    sim.autotune(2)
-    sim.step(20)
+    _, ref = make_pair(w)
     ref.step(20)
+    return w, ref
+
+
+@gpu
+@pytest.mark.parametrize("tuned", [False, True], ids=["default-shape", "autotuned"])
+def test_many_disks_full_size_20_steps(tuned, many_disks_oracle_20):
+    """The benched workload at full size (1024x4096, 500 disks, graph replay)
+    against the oracle for 20 steps, in the default kernel shape (the launch
+    configuration the bench times) and in the autotuner's pick."""
+    w, ref = many_disks_oracle_20
+    sim = lbm.from_workloads([w])
+    sim.set_graphs(16)
+    if tuned:
+        sim.autotune(2)
+    sim.step(20)
     sim.sync()
     cf = compare_fields(sim, ref)
     cp = compare_particles(sim, ref)
+    sim.close()
     assert cf["owner_equal"], cf
     assert cf["du"] < 2e-6, cf
     assert cp["count_equal"], cp
