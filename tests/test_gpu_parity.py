@@ -35,6 +35,7 @@ CASES_2D = [
     ((130, 17, 1), (0, 0, 1), 3),     # two tiles with a 2-node tail
     ((64, 40, 1), (1, 1, 1), 3),      # fully periodic
     ((200, 33, 1), (0, 1, 1), 4),     # walls in x, periodic in y
+    ((300, 20, 1), (1, 0, 1), 3),     # periodic x over three tiles, the last ragged: staged x-face wrap
 ]
 
 
@@ -69,7 +70,8 @@ def test_one_step_from_random_state_d2q9(case, vec):
 
 @gpu
 @pytest.mark.parametrize("n,per", [((20, 18, 14), (1, 0, 1)), ((45, 12, 10), (0, 0, 0)),
-                                   ((16, 16, 16), (1, 1, 1))])
+                                   ((16, 16, 16), (1, 1, 1)),
+                                   ((100, 12, 10), (1, 0, 0))])  # two x tiles: staged x-face wrap
 @pytest.mark.parametrize("vec", [0, 1, 2, 4])
 def test_one_step_from_random_state_d3q19(n, per, vec):
     w = W.random_small(11 + vec, D=3, n=n, periodic=per, nparticles=2, rlo=2.5, rhi=3.4, tau=0.9,
