@@ -479,9 +479,10 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
 }
 
 Shape default_shape(int Q, int fp16) {
-    // TMA-staged pipeline: 8 consumer warps, 3 stages
+    // TMA-staged pipeline: D2Q9 8 consumer warps and 3 stages; D3Q19 4 warps and
+    // 2 stages (four blocks per SM fit in shared memory, against three with 3)
     if (Q == 9) return Shape{fp16 ? 8 : 4, 8, 1, 8, 1, 1, 3, 128};
-    return Shape{fp16 ? 4 : 2, 2, 2, 4, 1, 1, 3, 64};
+    return Shape{fp16 ? 4 : 2, 2, 2, 4, 1, 1, 2, 64};
 }
 
 int enqueue_fluid(lbm_ctx* ctx, int commit, cudaStream_t st) {
