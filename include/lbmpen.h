@@ -173,14 +173,21 @@ int lbm_autotune(lbm_ctx* ctx, int reps);
 /* Fluid-kernel shape.  vec = 0 is the TMA-staged pipeline (one producer warp
  * filling a ring of shared-memory stages by tensor copies, `warps` consumer
  * warps, tile rows 4 or 8); vec = 1/2/4 (FP32) or 2/4/8 (FP16) is the
- * register path with vec nodes per thread and `warps` warps per block. */
+ * register path with vec nodes per thread and `warps` warps per block.
+ * A new context starts in the TMA pipeline: D2Q9 with 8 rows, 8 warps and a
+ * 3-stage ring, D3Q19 with 4 rows, 4 warps and a 2-stage ring.
+ * lbm_set_kernel_shape keeps the current ring depth; lbm_autotune may change
+ * it. */
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);
 int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
 /* Kernel launches issued by one lbm_step(ctx, 1) (fluid + particle kernels). */
 int lbm_launches_per_step(const lbm_ctx* ctx);
-/* Fluid kernel alone, one launch, for timing: advances the populations of
- * every instance by one step exactly as lbm_step does (particles are not
- * moved).  Returns after enqueueing. */
+/* Fluid kernel alone, one launch, for timing: the same fused kernel and
+ * work as the fluid part of lbm_step, on the current state of every
+ * instance.  It writes into the spare population buffer and a scratch copy
+ * of the projection sums and does not swap buffers, so the state that the
+ * API exposes (populations, particles, tile lists) is unchanged.  Returns
+ * after enqueueing. */
 int lbm_fluid_step_only(lbm_ctx* ctx);
 long long lbm_steps_done(const lbm_ctx* ctx);
 long long lbm_total_nodes(const lbm_ctx* ctx);
