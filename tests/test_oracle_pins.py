@@ -384,6 +384,50 @@ def test_poiseuille_startup_transient(oracle):
     assert np.abs(ux - exact).max() < 1e-3 * exact.max()
 
 
+def _couette(oracle, D, tau, u_lo, u_hi, H, steps, comp=0):
+    """Steady flow between two walls moving along axis `comp` (x, or z in 3D)
+    with velocities u_lo (plane y = -1/2) and u_hi (plane y = H - 1/2)."""
+    wall = np.zeros((3, 2, 3))
+    wall[1, 0, comp], wall[1, 1, comp] = u_lo, u_hi
+    n = (2, H, 1) if D == 2 else (2, H, 2)
+    s = oracle.Sim(oracle.make_config(D=D, n=n, periodic=(1, 0, 1), tau=tau, wall_u=wall))
+    s.step(steps)
+    u, _, _ = s.fields()
+    return (u[:, 0, :] if D == 2 else u[0, :, 0, :])  # [y, D]
+
+
+@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("tau,steps", [(0.6, 30000), (0.8, 20000), (1.0, 20000), (1.7, 12000)])
+@pytest.mark.parametrize("u_lo,u_hi", [(-5e-3, 5e-3), (0.0, 1e-2), (3e-3, -7e-3)])
+def test_moving_wall_couette_closed_form(oracle, D, tau, steps, u_lo, u_hi):
+    """Plane Couette flow under halfway bounce-back with the moving-wall term
+    (reading of the wall treatment: planes at -1/2 and H - 1/2).  The steady
+    profile is the straight line through the wall velocities at the planes,
+      u_x(y) = u_lo + (u_hi - u_lo) (y + 1/2) / H,
+    exact for the BGK lattice at any tau (the linear profile makes the
+    second-order Chapman-Enskog terms vanish and halfway bounce-back of a linear
+    field is exact), so it holds to round-off.  It fixes the wall term itself,
+    not only a ratio: a wrong factor, sign or power of cs^2 in
+    2 w_a (c_a . u_w) / cs^2 moves the line's ends."""
+    H = 16
+    u = _couette(oracle, D, tau, u_lo, u_hi, H, steps)
+    y = np.arange(H)
+    exact = u_lo + (u_hi - u_lo) * (y + 0.5) / H
+    scale = max(abs(u_lo), abs(u_hi))
+    assert np.abs(u[:, 0] - exact).max() < 1e-12 * scale
+    assert np.abs(u[:, 1:]).max() < 1e-13 * scale  # no wall-normal or spanwise flow
+
+
+def test_moving_wall_couette_spanwise_3d(oracle):
+    """The same closed form with the walls moving along z in D3Q19 (the edge
+    velocities with c_z != 0 carry the wall term)."""
+    H = 16
+    u = _couette(oracle, 3, 0.9, 2e-3, -6e-3, H, 20000, comp=2)
+    exact = 2e-3 + (-6e-3 - 2e-3) * (np.arange(H) + 0.5) / H
+    assert np.abs(u[:, 2] - exact).max() < 1e-12 * 6e-3
+    assert np.abs(u[:, :2]).max() < 1e-13 * 6e-3
+
+
 def _slab(oracle, tau, alpha, steps=30000, ny=60, y1=20, y2=40):
     wall = np.zeros((3, 2, 3))
     wall[1, 0, 0], wall[1, 1, 0] = -5e-6, 5e-6
