@@ -30,18 +30,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "liblbm_oracle_omp.so")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no contraction of multiply-adds)."""
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (no contraction of multiply-adds).
+
+    parallel=False: the parity build, single-threaded.  parallel=True: the
+    same source with -fopenmp, whose per-node loops run on all host cores
+    (identical results; used for the timed CPU baseline and long runs)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
+    out = _LIB_OMP if parallel else _LIB
     src_m = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC[:-2] + ".h"))
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < src_m:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+    if force or not os.path.exists(out) or os.path.getmtime(out) < src_m:
+        tmp = out + f".tmp{os.getpid()}"
+        omp = ["-fopenmp"] if parallel else []
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", *omp,
                                _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class Config(C.Structure):
@@ -53,16 +60,16 @@ class Config(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(parallel: bool = False):
+    """The parity build (default) or the OpenMP build of the oracle."""
+    if parallel not in _libs:
+        L = C.CDLL(build(parallel=parallel))
         L.orc_lattice.argtypes = [C.c_int, _ip, _dp, _ip]
         L.orc_feq.argtypes = [C.c_int, _dp, C.c_double, _dp]
         L.orc_force.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp]
@@ -85,8 +92,15 @@ def lib():
         L.orc_rigid_projection.argtypes = [C.c_void_p, _dp, _dp, _dp, _lp]
         L.orc_steps_done.argtypes = [C.c_void_p]
         L.orc_steps_done.restype = C.c_long
-        _lib = L
-    return _lib
+        L.orc_threads.argtypes = []
+        L.orc_threads.restype = C.c_int
+        _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the per-node loops of that build run on."""
+    return lib(parallel).orc_threads()
 
 
 def _v3(v):
@@ -173,19 +187,23 @@ def _ptr(a):
 class Sim:
     """One oracle simulation (owns the C state)."""
 
-    def __init__(self, cfg: Config):
+    def __init__(self, cfg: Config, parallel: bool = False):
+        """parallel=True runs the per-node loops on all host cores (the OpenMP
+        build of the same source: identical results)."""
+        self._L = lib(parallel)
+        self.parallel = parallel
         self.cfg = cfg
         self.D = cfg.D
         self.Q = 9 if cfg.D == 2 else 19
         self.n = tuple(cfg.n[d] for d in range(3))
         self.N = self.n[0] * self.n[1] * self.n[2]
-        self._h = lib().orc_create(C.byref(cfg))
+        self._h = self._L.orc_create(C.byref(cfg))
         if not self._h:
             raise ValueError("oracle: bad config")
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -205,30 +223,30 @@ class Sim:
         ratio = np.ascontiguousarray(ratio, np.float64).ravel()
         vel = None if vel is None else np.ascontiguousarray(vel, np.float64).ravel()
         omega = None if omega is None else np.ascontiguousarray(omega, np.float64).ravel()
-        lib().orc_add_particles(self._h, len(R), pos, R, ratio, _ptr(vel), _ptr(omega))
+        self._L.orc_add_particles(self._h, len(R), pos, R, ratio, _ptr(vel), _ptr(omega))
         self._keep = (vel, omega)
 
     @property
     def np(self):
-        return lib().orc_num_particles(self._h)
+        return self._L.orc_num_particles(self._h)
 
     def set_f(self, f):
-        lib().orc_set_f(self._h, np.ascontiguousarray(f, np.float64).reshape(-1))
+        self._L.orc_set_f(self._h, np.ascontiguousarray(f, np.float64).reshape(-1))
 
     def get_f(self):
         f = np.zeros(self.Q * self.N)
-        lib().orc_get_f(self._h, f)
+        self._L.orc_get_f(self._h, f)
         return f.reshape((self.Q,) + self.shape)
 
     def set_static_solid(self, mask):
         if mask is None:
-            lib().orc_set_static_solid(self._h, None)
+            self._L.orc_set_static_solid(self._h, None)
         else:
             m = np.ascontiguousarray(mask, np.int32).reshape(-1)
-            lib().orc_set_static_solid(self._h, m.ctypes.data_as(C.c_void_p))
+            self._L.orc_set_static_solid(self._h, m.ctypes.data_as(C.c_void_p))
 
     def step(self, n=1):
-        st = lib().orc_step(self._h, int(n))
+        st = self._L.orc_step(self._h, int(n))
         if st != 0:
             raise RuntimeError(f"oracle step failed with status {st}")
 
@@ -237,20 +255,20 @@ class Sim:
         u = np.zeros(self.N * 3)
         p = np.zeros(self.N)
         o = np.zeros(self.N, np.int32)
-        lib().orc_fields(self._h, u, p, o)
+        self._L.orc_fields(self._h, u, p, o)
         return (u.reshape(self.shape + (3,))[..., : self.D], p.reshape(self.shape),
                 o.reshape(self.shape))
 
     def owner_map(self):
         o = np.zeros(self.N, np.int32)
-        lib().orc_owner_map(self._h, o)
+        self._L.orc_owner_map(self._h, o)
         return o.reshape(self.shape)
 
     def particles(self):
         n = self.np
         out = {k: np.zeros((n, 3)) for k in ("X", "U", "W", "theta", "A")}
         cnt = np.zeros(n, np.int64)
-        lib().orc_get_particles(self._h, *(_ptr(out[k]) for k in ("X", "U", "W", "theta", "A")),
+        self._L.orc_get_particles(self._h, *(_ptr(out[k]) for k in ("X", "U", "W", "theta", "A")),
                                 _ptr(cnt))
         out["count"] = cnt
         return out
@@ -261,7 +279,7 @@ class Sim:
             v = kw.get(k)
             arrs.append(None if v is None else np.ascontiguousarray(v, np.float64).reshape(-1, 3))
         self._keep2 = arrs
-        lib().orc_set_particles(self._h, *(_ptr(a) for a in arrs))
+        self._L.orc_set_particles(self._h, *(_ptr(a) for a in arrs))
 
     def rigid_projection(self, u):
         """Eq. 22 over the current owner map for a velocity field u [..., D]."""
@@ -271,10 +289,10 @@ class Sim:
         U = np.zeros((n, 3))
         W = np.zeros((n, 3))
         cnt = np.zeros(n, np.int64)
-        lib().orc_rigid_projection(self._h, np.ascontiguousarray(u3).reshape(-1), U.reshape(-1),
+        self._L.orc_rigid_projection(self._h, np.ascontiguousarray(u3).reshape(-1), U.reshape(-1),
                                    W.reshape(-1), cnt)
         return U, W, cnt
 
     @property
     def steps(self):
-        return lib().orc_steps_done(self._h)
+        return self._L.orc_steps_done(self._h)

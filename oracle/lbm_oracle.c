@@ -8,6 +8,13 @@
  * the CUDA path.  Build with -ffp-contract=off so no multiply-add is fused
  * (the solid indicator test below must be evaluated with separate roundings).
  *
+ * The per-node loops of streaming, the moments and the collision carry
+ * OpenMP pragmas.  The parity build ignores them (single-threaded); a second
+ * build with -fopenmp runs those loops on all host cores for the timed CPU
+ * baseline and long reference runs.  Each node's arithmetic is the same in
+ * both builds and every sum over nodes (Eq. 22) stays serial, so the two
+ * builds give identical results.
+ *
  * One time step (state: post-collision f*, particles X^n, U^{n-1}, w^{n-1}, A^n):
  *   1. solid indicator chi^n / owner map from X^n (Eq. 9, lowest index wins);
  *   2. pull streaming with halfway bounce-back (Eq. 10, left-hand side);
@@ -25,6 +32,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define CS2 (1.0 / 3.0) /* lattice sound speed squared, c_s = c / sqrt(3) (Sec. 2.2) */
 
@@ -302,6 +312,7 @@ static void stream(orc_sim* s) {
     const int(*cv)[3] = lattice_c(c->D);
     const double* w = lattice_w(c->D);
     const int* opp = lattice_opp(c->D);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < c->n[2]; ++k)
         for (int j = 0; j < c->n[1]; ++j)
             for (int i = 0; i < c->n[0]; ++i) {
@@ -516,8 +527,9 @@ static int particle_update(orc_sim* s, const double* Un, const double* Wn) {
 static void macroscopic(orc_sim* s, double* p_out) {
     build_owner(s);
     stream(s);
-    double fl[19];
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < s->N; ++x) {
+        double fl[19];
         for (int q = 0; q < s->Q; ++q) fl[q] = s->fs[q * s->N + x];
         node_accel(s, x, s->a + 3 * x);
         double p;
@@ -530,12 +542,13 @@ int orc_step(orc_sim* s, int nsteps) {
     int D = s->c.D, Q = s->Q;
     double* Un = (double*)malloc(sizeof(double) * 3 * (s->np > 0 ? s->np : 1));
     double* Wn = (double*)malloc(sizeof(double) * 3 * (s->np > 0 ? s->np : 1));
-    double fl[19], feq[19], F[19], S[19];
     int status = 0;
     for (int it = 0; it < nsteps && status == 0; ++it) {
         macroscopic(s, NULL);
         if (s->np > 0) projection(s, s->u, Un, Wn, s->count);
+#pragma omp parallel for schedule(static)
         for (long x = 0; x < s->N; ++x) {
+            double fl[19], feq[19], F[19], S[19];
             double* ux = s->u + 3 * x;
             double p;
             for (int q = 0; q < Q; ++q) fl[q] = s->fs[q * s->N + x];
@@ -586,4 +599,13 @@ void orc_set_particles(orc_sim* s, const double* X, const double* U, const doubl
     if (W) memcpy(s->W, W, sz);
     if (theta) memcpy(s->theta, theta, sz);
     if (A) memcpy(s->A, A, sz);
+}
+
+/* threads the per-node loops run on: 1 in the parity build */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

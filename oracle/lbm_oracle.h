@@ -76,6 +76,8 @@ void     orc_set_particles(orc_sim* s, const double* X, const double* U, const d
 /* reductions of Eq. 22 over the current owner map of a given velocity field u (N*3) */
 void     orc_rigid_projection(orc_sim* s, const double* u, double* U, double* W, long* count);
 long     orc_steps_done(const orc_sim* s);
+/* threads of the per-node loops (1 unless built with OpenMP) */
+int      orc_threads(void);
 
 #ifdef __cplusplus
 }
