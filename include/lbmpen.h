@@ -88,7 +88,9 @@ typedef struct {
     double eps_p, eps_w;     /* stiffnesses epsilon_p, epsilon_w; defaults 2 and 1 */
     int K;                   /* predictor-corrector sub-steps (Algorithm 1); default 1 */
     int max_particles;       /* capacity reserved at creation; default 64 */
-    double max_radius;       /* largest particle radius to be added, <= 120; default 16 */
+    double max_radius;       /* largest particle radius to be added: 2 .. 120 (D2Q9) or
+                                2 .. 40 (D3Q19), the bounds of the exact integer sums of
+                                Eq. 22; default 16 */
     int fp16_scale_log2;     /* FP16 storage keeps f * 2^k (exact scaling); default 14 */
 } lbm_config;
 
@@ -180,6 +182,16 @@ int lbm_autotune(lbm_ctx* ctx, int reps);
  * it. */
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);
 int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
+/* Bound on each wait of the particle kernel at its grid-wide barrier between
+ * the phases of a step (projection, sub-steps of Algorithm 1); default 2 s.  A
+ * wait that runs out records LBM_ERR_TIMEOUT, the kernel returns, lbm_sync
+ * reports it and the context then refuses further work (LBM_ERR_STATE).
+ * With 0 s a block that does not find the barrier open on its first look
+ * gives up at once: with more than one particle block (more than 8
+ * particles) a step then times out for certain, which exercises the timeout
+ * path without a stalled GPU.  The fluid kernel's waits keep their own 2 s
+ * bound.  seconds in [0, 60]. */
+int lbm_set_particle_wait_limit(lbm_ctx* ctx, double seconds);
 /* Kernel launches issued by one lbm_step(ctx, 1) (fluid + particle kernels). */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 /* Fluid kernel alone, one launch, for timing: the same fused kernel and
@@ -206,8 +218,8 @@ long long lbm_total_nodes(const lbm_ctx* ctx);
  *   u   device, dim * N floats [d][z][y][x] (the layout of lbm_get_fields);
  *   np  particles, 0 .. LBM_NOALLOC_MAX_PARTICLES (more: LBM_ERR_INVALID);
  *   pos device, np * dim doubles; radius device, np doubles, each in
- *       [0, max_radius] with max_radius <= 120 (and 2 max_radius + 4 <= n on
- *       periodic axes);
+ *       [0, max_radius] with max_radius <= 120 for dim 2 and <= 40 for dim 3
+ *       (and 2 max_radius + 4 <= n on periodic axes);
  *   vel device out, np * dim doubles; omega device out, np (2D) or np * 3
  *       doubles; count device out, np ints (nodes owned by each particle);
  *   stream cudaStream_t the work is issued on.
@@ -216,8 +228,14 @@ long long lbm_total_nodes(const lbm_ctx* ctx);
  * array for that device; make that first call outside any stream capture.
  * Every call uses the same array, so calls that overlap on the GPU (other
  * streams, other host threads) race and give wrong results.  Returns
- * LBM_ERR_INVALID for a radius above max_radius and LBM_ERR_CAPACITY when a
- * particle overlaps more than 64 particles of lower index. */
+ * LBM_ERR_INVALID for a radius above max_radius, LBM_ERR_DIVERGED when a
+ * velocity on a counted node is non-finite or |u| >= 1/2 (the range of the
+ * exact fixed-point sums), LBM_ERR_CAPACITY when a particle
+ * overlaps more than 64 particles of lower index, and LBM_ERR_PARTICLE when a
+ * particle owns no node or its nodes have no rotational inertia (a radius
+ * below 1 can do either); such a particle gets U = omega = 0 and its count.
+ * Earlier codes in this list take precedence; on any error the outputs of
+ * the other particles are still written. */
 #define LBM_NOALLOC_MAX_PARTICLES 4096
 int lbm_rigid_projection_noalloc(int dim, const int* n, const int* periodic, const float* u, int np,
                                  const double* pos, const double* radius, double max_radius,

@@ -28,7 +28,8 @@ cudaError_t launch_unpack(int Q, int fp16, const InstDesc* insts, int inst, long
                           float* dst, cudaStream_t st);
 int particle_blocks_resident(int num_sms);
 cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int K,
-                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st);
+                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st,
+                             long long wait_ns);
 cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int lpar,
                            const Shape& sh, cudaStream_t st);
 int tma_tile_width(int Q);
@@ -113,6 +114,7 @@ struct lbm_ctx {
     bool failed = false;
     std::string err;
     AdjCtx adj;
+    long long wait_ns = -1;  // bound of the particle kernel's barrier waits; < 0: the default 2 s
 };
 
 namespace {
@@ -189,8 +191,8 @@ int validate(const lbm_config* c, char* why, size_t nwhy) {
     if (c->max_particles < 0 || c->max_particles > (1 << 20)) return bad("max_particles out of range");
     if ((double)c->n[0] * c->n[1] * c->n[2] * 19 > 2.0e9)
         return bad("at most 2e9 stored populations per instance");
-    if (!(c->max_radius >= 2.0) || c->max_radius > MAX_RADIUS)
-        return bad("max_radius must lie in [2, 120]");
+    if (!(c->max_radius >= 2.0) || c->max_radius > (D == 3 ? MAX_RADIUS_3D : MAX_RADIUS))
+        return bad(D == 3 ? "max_radius must lie in [2, 40] for D3Q19" : "max_radius must lie in [2, 120]");
     if (c->fp16_scale_log2 < 0 || c->fp16_scale_log2 > 24) return bad("fp16_scale_log2 in 0 .. 24");
     for (int d = 0; d < 3; ++d) {
         if (c->bc[d] != LBM_PERIODIC && c->bc[d] != LBM_WALL) return bad("bc must be PERIODIC or WALL");
@@ -508,7 +510,8 @@ int enqueue_step(lbm_ctx* ctx, cudaStream_t st) {
         const int K = ctx->inst[0].cfg.K;
         const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
         CK(launch_particles(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
-                            K, ctx->par ^ 1, ctx->shape, P<GridBar>(ctx->d_gridbar), fused, st));
+                            K, ctx->par ^ 1, ctx->shape, P<GridBar>(ctx->d_gridbar), fused, st,
+                            ctx->wait_ns));
     }
     ctx->par ^= 1;
     ctx->steps += 1;
@@ -1052,6 +1055,16 @@ int lbm_set_graphs(lbm_ctx* ctx, int steps_per_graph) {
     return LBM_OK;
 }
 
+int lbm_set_particle_wait_limit(lbm_ctx* ctx, double seconds) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!(seconds >= 0.0) || seconds > 60.0)
+        return set_err(ctx, LBM_ERR_INVALID, "the wait limit must lie in [0, 60] s%s");
+    ctx->wait_ns = (long long)(seconds * 1e9);
+    invalidate_graphs(ctx);  // captured launches carry the old bound
+    return LBM_OK;
+}
+
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps) {
     if (!ctx) return LBM_ERR_INVALID;
     if (vec) *vec = ctx->shape.tma ? 0 : ctx->shape.vec;
@@ -1427,7 +1440,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
                                 sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), st));
             if (ctx->np_total > 0)
                 CK(launch_particles(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, K, par ^ 1, sh,
-                                    P<GridBar>(ctx->d_gridbar), fused, st));
+                                    P<GridBar>(ctx->d_gridbar), fused, st, ctx->wait_ns));
         }
         for (int k = len - 1; k >= 0; --k) {
             CK(launch_adj_particles(ctx->D, dI, P<AdjPart>(A.d_apt) + (size_t)k * ni, P<AdjBufs>(A.d_abufs), ni,

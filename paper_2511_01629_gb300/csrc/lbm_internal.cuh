@@ -85,12 +85,19 @@ template <> struct Lat<19> {
 //   10-12 sum u, 13-15 sum d x u;  d = node - floor(X) (integer offsets),
 //   u in fixed point round(u * 2^FXBITS).  Integer sums are exact and do not
 //   depend on the order of addition, so the reductions are deterministic;
-//   they are converted to FP64 once per particle.  With |u| < 1/2 (larger
-//   velocities stop the run as diverged) and radii <= MAX_RADIUS the largest
-//   particle total stays below 2^62.
+//   they are converted to FP64 once per particle.  The additions wrap modulo
+//   2^64, so a partial or an intermediate total may overflow and the final
+//   total is still exact whenever it fits in int64.  It does under these
+//   bounds, with |u| < 1/2 (a larger speed stops the run as diverged) and
+//   |d| < R + 2 on a particle's n nodes (n < pi (R + 1)^2 in 2D,
+//   4/3 pi (R + 1)^3 in 3D): the largest total, a component of sum d x u, is
+//   below n (R + 2) 2^(FXBITS - 1), under 2^62 for R <= MAX_RADIUS = 120 in 2D
+//   and under 2^63 for R <= MAX_RADIUS_3D = 40 in 3D; a 3D sphere of radius
+//   120 (7.2e6 nodes) could reach 2^68, so larger spheres are refused.
 constexpr int NPV = 16;
 constexpr int FXBITS = 40;
-constexpr double MAX_RADIUS = 120.0;
+constexpr double MAX_RADIUS = 120.0;     // largest disk radius (2D)
+constexpr double MAX_RADIUS_3D = 40.0;   // largest sphere radius (3D)
 constexpr int LIST_CAP = 64;   // particles listed per tile (overflow -> LBM_ERR_CAPACITY)
 constexpr int KBITS = 10;      // list entry = particle << KBITS | slot
 constexpr int MAXK = 1 << KBITS;

@@ -11,7 +11,8 @@
 // allocator.
 //
 // Limits: at most LBM_NOALLOC_MAX_PARTICLES particles, radii <= 120 lattice
-// units.  Every call uses the same array: calls that overlap on the GPU (on
+// units in 2D and <= 40 in 3D (the bounds under which the exact integer sums
+// fit in 64 bits).  Every call uses the same array: calls that overlap on the GPU (on
 // different streams, or from several host threads) race and give wrong sums.
 // The array stays allocated on every GPU that loads the library until the
 // process exits.
@@ -121,7 +122,15 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_accumulate(NaGrid g, const floa
             if (mine) {
                 const long long node = ((long long)xyz[2] * g.n[1] + xyz[1]) * g.n[0] + xyz[0];
                 long long ux[3] = {0, 0, 0};
-                for (int d = 0; d < D; ++d) ux[d] = to_fx(u[d * N + node]);
+                float uu = 0.f;
+                for (int d = 0; d < D; ++d) {
+                    const float v = u[d * N + node];
+                    uu = fmaf(v, v, uu);
+                    ux[d] = to_fx(v);
+                }
+                // the speed bound of the exact sums, as in the fused kernel's
+                // divergence test (true for NaN too; to_fx would clamp silently)
+                if (!(uu < 0.25f)) atomicOr(reinterpret_cast<unsigned long long*>(scratch + NA_ERR), 4ull);
                 icnt = 1;
                 for (int d = 0; d < 3; ++d) id[d] = dd[d];
                 idd[0] = dd[0] * dd[0]; idd[1] = dd[1] * dd[1]; idd[2] = dd[2] * dd[2];
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_accumulate(NaGrid g, const floa
 
 // U = sum u / n and the angular velocity from the moments about floor(X),
 // as in the context path's finalisation.
-__global__ void k_na_finalize(int D, int np, const double* __restrict__ X, const long long* scratch,
+__global__ void k_na_finalize(int D, int np, const double* __restrict__ X, long long* scratch,
                               double* U, double* W, int* count) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
@@ -165,11 +174,15 @@ __global__ void k_na_finalize(int D, int np, const double* __restrict__ X, const
         Sl[d] = (double)v[13 + d] * scale;
     }
     count[p] = (int)v[0];
-    if (v[0] == 0) {
+    auto degenerate = [&]() {  // no node, or a node set without rotational inertia
+        atomicOr(reinterpret_cast<unsigned long long*>(scratch + NA_ERR), 8ull);
         for (int d = 0; d < D; ++d) U[p * D + d] = 0.0;
         if (D == 2) W[p] = 0.0;
         else
             for (int d = 0; d < 3; ++d) W[p * 3 + d] = 0.0;
+    };
+    if (v[0] == 0) {
+        degenerate();
         return;
     }
     for (int d = 0; d < D; ++d) U[p * D + d] = Su[d] / cnt;
@@ -184,7 +197,12 @@ __global__ void k_na_finalize(int D, int np, const double* __restrict__ X, const
         rr[j][i] = val;
     }
     if (D == 2) {
-        W[p] = Lv[2] / (rr[0][0] + rr[1][1]);
+        const double Izz = rr[0][0] + rr[1][1];
+        if (!(Izz > 0.0)) {
+            degenerate();
+            return;
+        }
+        W[p] = Lv[2] / Izz;
         return;
     }
     const double tr = rr[0][0] + rr[1][1] + rr[2][2];
@@ -194,6 +212,10 @@ __global__ void k_na_finalize(int D, int np, const double* __restrict__ X, const
     const double det = I[0][0] * (I[1][1] * I[2][2] - I[1][2] * I[2][1]) -
                        I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
                        I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
+    if (!(det > 0.0)) {  // I is positive semi-definite; singular for collinear node sets
+        degenerate();
+        return;
+    }
     for (int col = 0; col < 3; ++col) {
         double M[3][3];
         for (int r = 0; r < 3; ++r)
@@ -239,7 +261,7 @@ extern "C" int lbm_rigid_projection_noalloc(int dim, const int* n, const int* pe
     if (np > NA_MAXP) return LBM_ERR_INVALID;  // beyond the fixed scratch array
     if (np == 0) return LBM_OK;
     if (!u || !pos || !radius || !vel || !omega || !count) return LBM_ERR_INVALID;
-    if (!(max_radius >= 0.0) || max_radius > MAX_RADIUS) return LBM_ERR_INVALID;
+    if (!(max_radius >= 0.0) || max_radius > (dim == 3 ? MAX_RADIUS_3D : MAX_RADIUS)) return LBM_ERR_INVALID;
     NaGrid g;
     g.D = dim;
     for (int d = 0; d < 3; ++d) {
@@ -267,6 +289,8 @@ extern "C" int lbm_rigid_projection_noalloc(int dim, const int* n, const int* pe
         cudaStreamSynchronize(st) != cudaSuccess)
         return LBM_ERR_CUDA;
     if (err & 1) return LBM_ERR_INVALID;   // a radius above max_radius
+    if (err & 4) return LBM_ERR_DIVERGED;  // a velocity component is non-finite or |u| >= 1/2
     if (err & 2) return LBM_ERR_CAPACITY;  // a particle overlaps more than 64 of lower index
+    if (err & 8) return LBM_ERR_PARTICLE;  // a particle owns no node, or its nodes have no inertia
     return LBM_OK;
 }

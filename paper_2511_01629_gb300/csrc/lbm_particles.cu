@@ -335,7 +335,10 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
 }
 
 // ------------------------------------------------------------- the kernel --
-constexpr unsigned long long PWAIT_NS = 2000000000ull;  // 2 s bound on a barrier wait
+// Default bound on a barrier wait (2 s); a context may set another
+// (lbm_set_particle_wait_limit), 0 included: then a block that does not find
+// the barrier open on its first look gives up at once.
+constexpr unsigned long long PWAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -344,9 +347,10 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // Barrier over all blocks of the particle kernel (launched only when they are
-// all resident).  Bounded: after PWAIT_NS it records a timeout and returns
-// false, and the kernel stops.
-__device__ bool grid_sync(GridBar* gb, int* status) {
+// all resident).  Bounded: after limit_ns it records a timeout and returns
+// false, and the kernel stops.  Every block arrives before it waits, so the
+// last arrival always resets the count, timeouts included.
+__device__ bool grid_sync(GridBar* gb, int* status, unsigned long long limit_ns) {
     if (gridDim.x == 1) {  // one block: the block barrier is the grid barrier
         __syncthreads();
         return true;
@@ -364,7 +368,7 @@ __device__ bool grid_sync(GridBar* gb, int* status) {
         } else {
             const unsigned long long t0 = gtimer();
             while (*vgen == g) {
-                if (gtimer() - t0 > PWAIT_NS) {
+                if (gtimer() - t0 >= limit_ns) {
                     ok = 0;
                     atomicOr(status, ST_TIMEOUT);
                     break;
@@ -485,7 +489,7 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
 __global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ insts,
                                                    const PartRef* __restrict__ refs, int ntotal,
                                                    int D, int K, int first, int last, int lpar,
-                                                   Shape sh, GridBar* gb) {
+                                                   Shape sh, GridBar* gb, unsigned long long wait_ns) {
     __shared__ long long tot[PB][NPV];
     __shared__ double sF[PB][6];
     __shared__ AxisTiles sAT[PB][3];
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ 
     stage_desc(&sdesc, insts[refs[gp0].inst]);  // blocks never straddle instances
     const InstDesc& in = sdesc;
     for (int ph = first; ph <= last; ++ph) {
-        if (ph > first && !grid_sync(gb, in.status)) return;
+        if (ph > first && !grid_sync(gb, in.status, wait_ns)) return;
         if (ph == 0) phase_finalize(in, refs, ntotal, D, gp0, tot);
         else phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == K, sh, xs, xs2, sF, sAT);
     }
@@ -531,14 +535,16 @@ int particle_blocks_resident(int num_sms) {
 // The particle part of a step: one launch with grid barriers when all blocks
 // fit on the GPU at once, else one launch per phase.
 cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int K,
-                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st) {
+                             int lpar, const Shape& sh, GridBar* gb, bool fused, cudaStream_t st,
+                             long long wait_ns) {
     const int blocks = (ntotal + PB - 1) / PB;
+    const unsigned long long lim = wait_ns < 0 ? PWAIT_NS : (unsigned long long)wait_ns;
     if (fused) {
-        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, 0, K, lpar, sh, gb);
+        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, 0, K, lpar, sh, gb, lim);
         return cudaGetLastError();
     }
     for (int ph = 0; ph <= K; ++ph)
-        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, ph, ph, lpar, sh, gb);
+        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, ph, ph, lpar, sh, gb, lim);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ def lib():
         "lbm_kernel_shape": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "lbm_set_kernel_shape": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
         "lbm_launches_per_step": (C.c_int, [_vp]),
+        "lbm_set_particle_wait_limit": (C.c_int, [_vp, C.c_double]),
         "lbm_fluid_step_only": (C.c_int, [_vp]),
         "lbm_steps_done": (C.c_longlong, [_vp]),
         "lbm_total_nodes": (C.c_longlong, [_vp]),
@@ -337,6 +338,9 @@ class LBM:
 
     def set_kernel_shape(self, vec, rows, warps):
         self._check(lib().lbm_set_kernel_shape(self._h, int(vec), int(rows), int(warps)))
+
+    def set_particle_wait_limit(self, seconds: float):
+        self._check(lib().lbm_set_particle_wait_limit(self._h, float(seconds)))
 
     def launches_per_step(self) -> int:
         return lib().lbm_launches_per_step(self._h)
