@@ -163,50 +163,47 @@ def traffic_per_launch(storage, workload, shape):
         return None
 
 
-def cpu_oracle_mlups(ws, steps):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+def oracle_sample(w, budget_s, min_steps=20, max_steps=100000, warmup=1):
+    """The FP64 oracle as it stands (its OpenMP build: the same arithmetic on
+    every host core) on a bounded sample of workload w: `warmup` untimed steps,
+    then as many timed steps as fit in about budget_s seconds (at least
+    min_steps).  Returns (MLUPS, steps, seconds, threads)."""
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from harness import oracle_config
-    w = ws[0]
-    sim = oracle.Sim(oracle_config(w))
+    sim = oracle.Sim(oracle_config(w), parallel=True)
     if w.num_particles:
         sim.add_particles(w.pos, w.radius, w.ratio)
-    sim.step(1)  # warm-up (page-in, first owner map)
     t0 = time.perf_counter()
-    sim.step(steps)
+    sim.step(max(1, warmup))  # page-in, first owner map
+    per = (time.perf_counter() - t0) / max(1, warmup)
+    k = int(min(max(min_steps, budget_s / max(per, 1e-6)), max_steps))
+    t0 = time.perf_counter()
+    sim.step(k)
     dt = time.perf_counter() - t0
-    return w.nodes * steps / dt / 1e6, dt
+    sim.close()
+    return w.nodes * k / dt / 1e6, k, dt, oracle.threads(True)
 
 
 def run_reference(args, ws_n, rank):
+    """The contract's reference arm: the FP64 oracle as it stands, on all host
+    cores, on this workload and metric; each timed step is one full oracle step
+    of instance 0, as many as fit in about 90 s (at most --steps)."""
     if rank != 0:
         return
     ws = make_workloads(args.workload, 0)
     w = ws[0]
-    budget = 90.0  # seconds of oracle work for the whole run
-    per_step = w.nodes / 4e6
-    k = max(1, min(args.steps, int(budget / per_step) - args.warmup))
-    w_steps = min(args.warmup, 2)
-    import oracle
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from harness import oracle_config
-    sim = oracle.Sim(oracle_config(w))
-    if w.num_particles:
-        sim.add_particles(w.pos, w.radius, w.ratio)
-    if w_steps:
-        sim.step(w_steps)
-    t0 = time.perf_counter()
-    sim.step(k)
-    dt = time.perf_counter() - t0
-    mlups = w.nodes * k / dt / 1e6
-    sample = f"{k} full oracle steps of instance 0 after {w_steps} warm-up steps"
+    w_steps = args.warmup
+    mlups, k, dt, cores = oracle_sample(w, 90.0, min_steps=1, max_steps=args.steps, warmup=w_steps)
+    sample = (f"{k} full FP64 oracle steps of instance 0 ({w.nodes} nodes) after {w_steps} untimed "
+              f"steps, {dt:.1f} s on {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws_n,
         "steps": k, "warmup": w_steps, "ms_per_step": dt / k * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": describe(args.workload, ws, "fp64"),
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -475,13 +472,13 @@ def main():
         line["adjoint"] = adj
     else:
         line["adjoint_forward_ratio"] = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws_c = make_workloads(args.workload, 0)
-        steps_c = 3 if ws_c[0].nodes > 1e6 else 20
-        mc, dtc = cpu_oracle_mlups(ws_c, steps_c)
-        line["cpu_baseline"] = {"value": mc, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                                "sample": f"{steps_c} FP64 oracle steps of instance 0 "
-                                          f"({ws_c[0].nodes} nodes), {dtc:.1f} s"}
+        mc, kc, dtc, cores = oracle_sample(ws_c[0], 15.0)
+        line["cpu_baseline"] = {"value": mc, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"{kc} full FP64 oracle steps of instance 0 "
+                                          f"({ws_c[0].nodes} nodes) after 1 untimed step, "
+                                          f"{dtc:.1f} s on {cores} threads"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

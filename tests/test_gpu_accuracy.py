@@ -72,6 +72,7 @@ def test_fp32_single_disk_1000_steps(single_case):
     assert cf["owner_equal"] and cp["count_equal"], (cf, cp)
     assert cf["du"] * cf["uref"] < 1e-6, cf   # in lattice units
     assert cf["du"] < 1e-6, cf                # relative to U_ref (measured 6.7e-7)
+    assert cf["dp_f"] < 1e-6, cf
     assert cp["dU"] < 1e-6 * cp["Uscale"], cp
 
 
@@ -81,6 +82,7 @@ def test_fp32_many_disks_100_steps(many_case):
     print("fp32 many", cf, cp)
     assert cf["owner_equal"] and cp["count_equal"], (cf, cp)
     assert cf["du"] < 1e-6, cf
+    assert cf["dp_f"] < 1e-6, cf
     assert cp["dU"] < 1e-6 * cp["Uscale"], cp
 
 
@@ -90,6 +92,7 @@ def test_fp16_storage_single_disk_1000_steps(single_case):
     print("fp16 single", cf, cp)
     assert cf["owner_equal"] and cp["count_equal"], (cf, cp)
     assert cf["du"] < 1e-3, cf                # measured 6.4e-4
+    assert cf["dp_f"] < 1e-3, cf
     assert cf["du"] * cf["uref"] < 1e-6, cf
 
 
@@ -99,6 +102,7 @@ def test_fp16_storage_many_disks_100_steps(many_case):
     print("fp16 many", cf, cp)
     assert cf["owner_equal"] and cp["count_equal"], (cf, cp)
     assert cf["du"] < 1e-3, cf
+    assert cf["dp_f"] < 1e-3, cf
 
 
 TERMINAL = dict(seed=5, nx=80, ny=320, radius=6.0, ratio=1.5)

@@ -62,6 +62,7 @@ def test_one_step_from_random_state_d2q9(case, vec):
     cf = compare_fields(sim, ref)
     assert cf["owner_equal"], cf
     assert cf["du"] < 2e-6, cf
+    assert cf["dp_f"] < 2e-6, cf
     cp = compare_particles(sim, ref)
     assert cp["count_equal"], cp
     assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-12), cp
@@ -88,6 +89,7 @@ def test_one_step_from_random_state_d3q19(n, per, vec):
     cf = compare_fields(sim, ref)
     assert cf["owner_equal"], cf
     assert cf["du"] < 2e-6, cf
+    assert cf["dp_f"] < 2e-6, cf
     cp = compare_particles(sim, ref)
     assert cp["count_equal"], cp
     assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-12), cp
@@ -106,6 +108,7 @@ def test_poiseuille_disk_2000_steps():
     cp = compare_particles(sim, ref)
     assert cf["owner_equal"], cf
     assert cf["du"] < 5e-6, cf
+    assert cf["dp_f"] < 5e-6, cf
     assert cf["du"] * cf["uref"] < 1e-6, cf
     assert cp["dX"] < 1e-4, cp
     assert cp["dU"] < 1e-6 * cf["uref"], cp
@@ -126,6 +129,7 @@ def test_moving_wall_couette():
     sim.sync()
     cf = compare_fields(sim, ref)
     assert cf["owner_equal"] and cf["du"] < 5e-6, cf
+    assert cf["dp_f"] < 5e-6, cf
 
 
 @gpu
@@ -149,6 +153,7 @@ def test_spheres3d_full_size_2_steps():
     ref.close()
     assert cf["owner_equal"], cf
     assert cf["du"] < 2e-6, cf
+    assert cf["dp_f"] < 2e-6, cf
     assert cp["count_equal"], cp
     assert cp["dU"] < 2e-6 * cp["Uscale"], cp
 
@@ -178,6 +183,7 @@ def test_ensemble_full_size_2_steps():
         ref.close()
         assert cf["owner_equal"], (i, cf)
         assert cf["du"] < 2e-6, (i, cf)
+        assert cf["dp_f"] < 2e-6, (i, cf)
         assert cp["count_equal"], (i, cp)
         assert cp["dU"] < 2e-6 * max(cp["Uscale"], 1e-30), (i, cp)
     sim.close()
@@ -198,6 +204,7 @@ def test_colliding_disks_match_oracle(K):
     cp = compare_particles(sim, ref)
     assert cf["owner_equal"], cf
     assert cf["du"] < 5e-6, cf
+    assert cf["dp_f"] < 5e-6, cf
     assert cp["count_equal"], cp
     assert cp["dU"] < 5e-6 * cp["Uscale"], cp
     assert cp["dX"] < 1e-6, cp
@@ -230,6 +237,7 @@ def test_many_disks_full_size_20_steps(tuned, many_disks_oracle_20):
     sim.close()
     assert cf["owner_equal"], cf
     assert cf["du"] < 2e-6, cf
+    assert cf["dp_f"] < 2e-6, cf
     assert cp["count_equal"], cp
     assert cp["dU"] < 2e-6 * cp["Uscale"], cp
     assert cp["dX"] < 1e-9, cp
