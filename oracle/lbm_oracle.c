@@ -475,7 +475,13 @@ void orc_collision_forces(const orc_config* cfg, int np, const double* X, const 
 
 /* Algorithm 1 (dt = 1) for all particles together, since F_col at each
    sub-step depends on every particle's position at that sub-step.  M is the
-   discrete mass rho_s * count^n.  Afterwards A^{n+1} (Algorithm 1, step 6),
+   discrete mass rho_s * count^n.  Afterwards A^{n+1} of Algorithm 1:
+   (2/dt^2)(X^{n+1} - X^n - dt Ubar) is, in exact arithmetic, twice the sum of
+   the K correction displacements dt^2/(2M) (dt/K)^2/2 ... (F1 + F2) that
+   Algorithm 1 adds to X^n + dt Ubar, and it is evaluated as that sum: the
+   printed difference of positions (~10^3) minus a displacement (~10^-5)
+   cancels catastrophically and would leave ulp(X) ~ 2e-13 of rounding noise
+   per step in A, which then acts as a force on the solid nodes.  Then
    the orientation theta^{n+1} = theta^n + (w^n + w^{n-1}) / 2 (the paper
    gives no rule; trapezoid like X), and U^{n-1} <- U^n.  Returns -1 when a
    particle centre has left the domain across a wall. */
@@ -488,6 +494,7 @@ static int particle_update(orc_sim* s, const double* Un, const double* Wn) {
         Ubar[i] = 0.5 * (Un[i] + s->U[i]);
         Xk[i] = s->X[i];
     }
+    double* corr = (double*)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
     double h = 1.0 / K;
     for (int k = 1; k <= K; ++k) {
         orc_collision_forces(&s->c, np, Xk, s->R, s->ratio, F1);
@@ -495,15 +502,18 @@ static int particle_update(orc_sim* s, const double* Un, const double* Wn) {
         orc_collision_forces(&s->c, np, Xs, s->R, s->ratio, F2);
         for (int p = 0; p < np; ++p) {
             double M = s->ratio[p] * s->c.rho_f * (double)s->count[p];
-            for (int d = 0; d < 3; ++d)
-                Xk[3 * p + d] = Xs[3 * p + d] + 1.0 / (2.0 * M) * h * h * 0.5 * (F1[3 * p + d] + F2[3 * p + d]);
+            for (int d = 0; d < 3; ++d) {
+                double c = 1.0 / (2.0 * M) * h * h * 0.5 * (F1[3 * p + d] + F2[3 * p + d]);
+                corr[3 * p + d] += c;
+                Xk[3 * p + d] = Xs[3 * p + d] + c;
+            }
         }
     }
     int status = 0;
     for (int p = 0; p < np; ++p) {
         for (int d = 0; d < 3; ++d) {
             int i = 3 * p + d;
-            s->A[i] = 2.0 * (Xk[i] - s->X[i] - Ubar[i]);
+            s->A[i] = 2.0 * corr[i]; /* = 2 (X^{n+1} - X^n - Ubar) in exact arithmetic */
             double xn = Xk[i];
             if (d < s->c.D) {
                 if (s->c.periodic[d]) {
@@ -519,7 +529,7 @@ static int particle_update(orc_sim* s, const double* Un, const double* Wn) {
             s->W[i] = Wn[i];
         }
     }
-    free(Ubar); free(Xk); free(Xs); free(F1); free(F2);
+    free(Ubar); free(Xk); free(Xs); free(F1); free(F2); free(corr);
     return status;
 }
 

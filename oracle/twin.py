@@ -226,12 +226,17 @@ class Twin:
         Xk = X
         h = 1.0 / self.K
         M = ratio * self.rho_f * count
+        corr = torch.zeros_like(X)
         for _ in range(self.K):
             F1 = self.collision_forces(Xk, R, ratio)
             Xs = Xk + h * Ubar
             F2 = self.collision_forces(Xs, R, ratio)
-            Xk = Xs + (1.0 / (2.0 * M))[:, None] * h * h * 0.5 * (F1 + F2)
-        Anew = 2.0 * (Xk - X - Ubar)
+            c = (1.0 / (2.0 * M))[:, None] * h * h * 0.5 * (F1 + F2)
+            corr = corr + c
+            Xk = Xs + c
+        # A^{n+1} = 2 (X^{n+1} - X^n - Ubar), evaluated as the sum of the
+        # corrections it equals (the difference of positions cancels)
+        Anew = 2.0 * corr
         cols = []
         for d in range(3):
             x = Xk[:, d]

@@ -482,7 +482,7 @@ def test_algorithm1_trapezoid_and_collision_acceleration(oracle):
         part = s.particles()
         M = ratio * part["count"][0]
         assert part["A"][0, 1] == pytest.approx(Fw[1] / (K * M), rel=1e-12 if K == 1 else 1e-9)
-        assert abs(part["A"][0, 0]) < 8 * np.spacing(20.0)  # round-off of 2(X1 - X0 - Ubar)
+        assert part["A"][0, 0] == 0.0  # no force along x: no correction, exactly
 
 
 def test_orientation_trapezoid(oracle):
@@ -496,3 +496,42 @@ def test_orientation_trapezoid(oracle):
     part = s.particles()
     assert abs(part["W"][0, 2]) < 1e-20
     assert part["theta"][0, 2] == pytest.approx(0.005, rel=1e-15)
+
+
+def test_collision_acceleration_vanishes_without_forces(oracle):
+    """Algorithm 1 with no collision force: X^{n+1} = X^n + Ubar, so A^{n+1} =
+    (2/dt^2)(X^{n+1} - X^n - dt Ubar) is exactly zero, at any position.  (Its
+    literal evaluation as a difference of positions of size ~10^3 would leave
+    ulp(X) ~ 1e-13 of rounding noise instead; the oracle evaluates the bracket
+    as the sum of the sub-step corrections it equals.)"""
+    for K in (1, 3):
+        s = oracle.Sim(oracle.make_config(D=2, n=(64, 1600, 1), periodic=(1, 0, 1), tau=1.0,
+                                          g_grav=(0, -2e-6), K=K))
+        s.add_particles([[31.3, 1280.123456789]], [12.0], [1.5], vel=[[1.234e-5, -3.21e-5]])
+        for _ in range(5):
+            s.step(1)
+            assert np.all(s.particles()["A"] == 0.0)
+
+
+def test_single_disk_is_insensitive_to_round_off(oracle):
+    """Without collisions the settling-disk dynamics damp small perturbations:
+    populations perturbed by 1e-12 (relative) stay within 1e-18 (absolute) of
+    the unperturbed run over 300 steps.  A rounding-noise force of ulp(X) per
+    step in A^{n+1} would instead decorrelate the two runs to ~1e-12 within
+    ~150 steps."""
+    w = W.single_disk(0, nx=100, ny=400, radius=8.0)
+    cfg = oracle.make_config(D=2, n=w.n, periodic=w.periodic, tau=w.tau, alpha=w.alpha,
+                             g_grav=w.g_grav)
+    sims = []
+    for eps in (0.0, 1e-12):
+        sim = oracle.Sim(cfg, parallel=True)
+        sim.add_particles(w.pos, w.radius, w.ratio)
+        sim.step(1)
+        if eps:
+            f = sim.get_f()
+            sim.set_f(f * (1 + eps * np.random.default_rng(0).standard_normal(f.shape)))
+        sims.append(sim)
+    for sim in sims:
+        sim.step(299)
+    d = np.abs(sims[1].fields()[0] - sims[0].fields()[0]).max()
+    assert d < 1e-18, d
