@@ -70,7 +70,7 @@ struct Instance {
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
     DevBuf f[2], prec, lcnt[2], lent[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
-        Ubar, Xf;
+        Ubar, Xf, Acor;
     std::vector<double> hR;      // radii (validation)
     std::vector<double> hratio;  // density ratios (per-particle constants)
 };
@@ -281,6 +281,7 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.count = P<int>(I.count);
     d.Xk = P<double>(I.Xk);
     d.Ubar = P<double>(I.Ubar);
+    d.Acor = P<double>(I.Acor);
     d.Xf = P<float>(I.Xf);
     d.pconst = P<double>(I.pconst);
     d.Xsf = P<float>(I.Xsf);
@@ -570,7 +571,7 @@ void destroy_all(lbm_ctx* ctx) {
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
                           &I.partial, &I.partial_scratch, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
-                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc};
+                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc, &I.Acor};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
     dfree(ctx, ctx->d_insts);
@@ -583,7 +584,7 @@ void destroy_all(lbm_ctx* ctx) {
 }
 
 int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
-    DevBuf* v3[] = {&I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.Ubar};
+    DevBuf* v3[] = {&I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.Ubar, &I.Acor};
     int rc;
     const size_t c = (size_t)std::max(cap, 1);
     for (DevBuf* b : v3)

@@ -165,6 +165,7 @@ struct InstDesc {
     int* count;               // [np]
     double* Xk;               // [2][np][3] Algorithm-1 sub-step positions
     double* Ubar;             // [np][3]
+    double* Acor;             // [np][3] sum of the sub-step corrections of Algorithm 1 (K > 1)
     float* Xf;                // [2][np][4] float copy of X^{k} (w = R) for the pair filter
     float* Xsf;               // [2][np][4] float copy of X^{k} + Ubar/K (w = R): predicted positions
     double* pconst;           // [np][8]: 1 - rho_f/rho_s, C/eps_p, C/eps_w, 1/delta,

@@ -252,8 +252,8 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
 // sub-step A^{n+1}, theta^{n+1}, U^{n-1} <- U^n and the record for the next
 // step.  Each lane evaluates the expressions of a serial loop over d.
 __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid, const double* F1in,
-                            const double* F2in, int src, double h, int last, int D, const Shape& sh,
-                            AxisTiles* at) {
+                            const double* F2in, int src, double h, int first, int last, int D,
+                            const Shape& sh, AxisTiles* at) {
     if (!valid) {  // in-range operands for the shuffle-only lanes; nothing is stored
         i = 0;
         d = 0;
@@ -262,7 +262,7 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
     const long long j = 3LL * i + d;
     // every operand up front, in one batch of loads
     const double X0 = in.Xk[(long long)src * in.np * 3 + j];
-    const double Ub = in.Ubar[j], Xold = in.X[j], Wn = in.Wn[j], Un = in.Un[j], Wo = in.W[j], Th = in.theta[j];
+    const double Ub = in.Ubar[j], Wn = in.Wn[j], Un = in.Un[j], Wo = in.W[j], Th = in.theta[j];
     double F1 = F1in[d], F2 = F2in[d];
     const double* pc = in.pconst + PCONST_N * i;
     const double invrhos = pc[PC_INVRHOS], cw = pc[PC_CWALL], idl = pc[PC_INVDELTA], Ri = pc[PC_R];
@@ -274,10 +274,15 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
     wall_force_d(in, d, X0, F1, cw, idl, Ri);
     wall_force_d(in, d, Xst, F2, cw, idl, Ri);
     const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
-    const double Xn = Xst + c * (F1 + F2);
+    const double cor = c * (F1 + F2);      // this sub-step's correction
+    const double Xn = Xst + cor;
+    // A^{n+1} = 2 (X^{n+1} - X^n - Ubar) is twice the sum of the corrections;
+    // summed directly, since the difference of positions cancels catastrophically
+    const double acc = first ? cor : in.Acor[j] + cor;
     const float Rf = (float)Ri;
     if (!last) {
         if (valid) {
+            in.Acor[j] = acc;
             in.Xk[(long long)dst * in.np * 3 + j] = Xn;
             float* xf = in.Xf + ((long long)dst * in.np + i) * 4;
             float* xsf = in.Xsf + ((long long)dst * in.np + i) * 4;
@@ -291,7 +296,7 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
         return;
     }
     bool left = false;
-    const double An = 2.0 * (Xn - Xold - Ub);
+    const double An = 2.0 * acc;
     double xn = Xn;
     if (d < D) {
         if (in.periodic[d]) {
@@ -427,7 +432,7 @@ __device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntot
 // the block's warps find the pair forces (one particle each), one thread per
 // particle does the FP64 update.
 __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
-                              int src, int K, int last, const Shape& sh, float4* xs, float4* xs2,
+                              int src, int K, int first, int last, const Shape& sh, float4* xs, float4* xs2,
                               double (*sF)[6], AxisTiles (*sAT)[3]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double h = in.hK;
@@ -476,7 +481,7 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
     if (warp == 0) {  // one lane per (particle, component)
         const int sl = lane & (PB - 1), d = lane / PB;
         const bool valid = d < 3 && gp0 + sl < ntotal && refs[gp0 + sl].inst >= 0;
-        update_lane(in, valid ? refs[gp0 + sl].p : 0, d, sl, valid, sF[sl], sF[sl] + 3, src, h, last, D, sh,
+        update_lane(in, valid ? refs[gp0 + sl].p : 0, d, sl, valid, sF[sl], sF[sl] + 3, src, h, first, last, D, sh,
                     sAT[sl]);
     }
 }
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ 
     for (int ph = first; ph <= last; ++ph) {
         if (ph > first && !grid_sync(gb, in.status, wait_ns)) return;
         if (ph == 0) phase_finalize(in, refs, ntotal, D, gp0, tot);
-        else phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == K, sh, xs, xs2, sF, sAT);
+        else phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == 1, ph == K, sh, xs, xs2, sF, sAT);
     }
     if (last == K) {
         __syncthreads();  // records and tile ranges of the block's particles are ready
