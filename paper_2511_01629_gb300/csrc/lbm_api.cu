@@ -34,7 +34,7 @@ cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntota
                            const Shape& sh, cudaStream_t st);
 int tma_tile_width(int Q);
 bool tma_rows_ok(int rows);
-int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages);
+int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages, int ninst);
 cudaError_t launch_fluid_tma(int Q, int fp16, const InstDesc* insts, const void* tmaps,
                              const uint16_t* tile_inst, int ntiles, int par, const Shape& sh,
                              int commit, int grid, int* tile_ctr, int stages, int ninst, cudaStream_t st);
@@ -69,7 +69,7 @@ struct Instance {
     int ntile[3] = {1, 1, 1};
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
-    DevBuf f[2], prec, lcnt[2], lent[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
+    DevBuf f[2], prec, lcnt[2], lent[2], lrec[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
         Ubar, Xf, Acor;
     std::vector<double> hR;      // radii (validation)
     std::vector<double> hratio;  // density ratios (per-particle constants)
@@ -81,7 +81,7 @@ struct AdjInst {
     std::vector<DevBuf> ckpt;   // [nseg] populations at the start of each segment
     DevBuf ckst;                // [nseg + 1][np][16] particle state at segment starts, then the final one
     std::vector<DevBuf> slot;   // [L + 1] populations entering each step of the segment
-    DevBuf rprec, rlcnt, rlent, rgeo, rstate;  // [L + 1] records of each step
+    DevBuf rprec, rlcnt, rlent, rlrec, rgeo, rstate;  // [L + 1] records of each step
     DevBuf fbar[2];             // adjoint of the pre-collision populations (ping-pong)
     DevBuf pbuf;                // adjoint particle arrays (AdjBufs)
 };
@@ -267,6 +267,8 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.list_cnt[1] = P<int>(I.lcnt[1]);
     d.list_ent[0] = P<uint32_t>(I.lent[0]);
     d.list_ent[1] = P<uint32_t>(I.lent[1]);
+    d.list_rec[0] = I.lrec[0].ptr;
+    d.list_rec[1] = I.lrec[1].ptr;
     d.partial = P<long long>(I.partial);
     d.partial_scratch = P<long long>(I.partial_scratch);
     d.X = P<double>(I.X);
@@ -383,7 +385,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 
 // Tensor map of one population buffer: the stored populations as a
 // [Q-1][nz][ny][pitch] tensor (x innermost, dim = nx so that boxes read
-// zeros beyond the last node), boxes of (tile width + 2 halo) x ty (x tz).
+// zeros beyond the last node).  D2Q9 boxes hold every population of a tile
+// with one halo row on each side, (tile width + 2 halo) x (ty + 2) x (Q - 1),
+// so a tile takes one copy; D3Q19 boxes hold one population's source rows,
+// (tile width + 2 halo) x ty x tz.
 int encode_pop_map(lbm_ctx* ctx, const Instance& I, void* ptr, CUtensorMap* out) {
     auto enc = tmap_encoder();
     if (!enc) return set_err(ctx, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available%s");
@@ -397,11 +402,12 @@ int encode_pop_map(lbm_ctx* ctx, const Instance& I, void* ptr, CUtensorMap* out)
     strides[0] = (cuuint64_t)I.pitch * ss;
     box[0] = (cuuint32_t)(ctx->shape.tw + 2 * halo);
     box[1] = (cuuint32_t)ctx->shape.ty;
-    if (ctx->D == 2) {
+    if (ctx->D == 2) {  // one box per tile: every population, rows y0 - 1 .. y0 + ty
         rank = 3;
         dims[2] = (cuuint64_t)(ctx->Q - 1);
         strides[1] = (cuuint64_t)I.pitch * I.n[1] * ss;
-        box[2] = 1;
+        box[1] = (cuuint32_t)(ctx->shape.ty + 2);
+        box[2] = (cuuint32_t)(ctx->Q - 1);
     } else {
         rank = 4;
         dims[2] = (cuuint64_t)I.n[2];
@@ -457,6 +463,7 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
         for (int b = 0; b < 2; ++b) {
             if ((rc = dalloc(ctx, I.lcnt[b], sizeof(int) * I.ntiles))) return rc;
             if ((rc = dalloc(ctx, I.lent[b], sizeof(uint32_t) * (size_t)I.ntiles * LIST_CAP))) return rc;
+            if ((rc = dalloc(ctx, I.lrec[b], (size_t)CAND_BYTES * I.ntiles * LIST_CAP))) return rc;
             CK(cudaMemsetAsync(I.lcnt[b].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
         }
         const size_t pb = sizeof(long long) * (size_t)std::max(I.cap, 1) * I.maxk * NPV;
@@ -471,7 +478,7 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
     CK(cudaMemcpyAsync(ctx->d_tile_inst.ptr, tab.data(), sizeof(uint16_t) * tab.size(),
                        cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    const int occ = sh.tma ? fluid_tma_blocks_per_sm(ctx->Q, ctx->fp16, sh, sh.stages)
+    const int occ = sh.tma ? fluid_tma_blocks_per_sm(ctx->Q, ctx->fp16, sh, sh.stages, (int)ctx->inst.size())
                            : fluid_max_blocks_per_sm(ctx->Q, ctx->fp16, sh);
     if (occ < 1) return set_err(ctx, LBM_ERR_INVALID, "kernel shape does not fit on an SM%s");
     ctx->grid = occ * ctx->num_sms;
@@ -484,7 +491,7 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
 Shape default_shape(int Q, int fp16) {
     // TMA-staged pipeline: D2Q9 8 consumer warps and 3 stages; D3Q19 4 warps and
     // 2 stages (four blocks per SM fit in shared memory, against three with 3)
-    if (Q == 9) return Shape{fp16 ? 8 : 4, 8, 1, 8, 1, 1, 3, 128};
+    if (Q == 9) return Shape{fp16 ? 8 : 4, 8, 1, 8, 1, 1, fp16 ? 3 : 2, 128};
     return Shape{fp16 ? 4 : 2, 2, 2, 4, 1, 1, 2, 64};
 }
 
@@ -556,7 +563,8 @@ void adj_release(lbm_ctx* ctx) {
     for (auto& a : A.ai) {
         for (auto& b : a.ckpt) dfree(ctx, b);
         for (auto& b : a.slot) dfree(ctx, b);
-        DevBuf* bufs[] = {&a.ckst, &a.rprec, &a.rlcnt, &a.rlent, &a.rgeo, &a.rstate, &a.fbar[0], &a.fbar[1], &a.pbuf};
+        DevBuf* bufs[] = {&a.ckst, &a.rprec, &a.rlcnt, &a.rlent, &a.rlrec, &a.rgeo, &a.rstate, &a.fbar[0],
+                          &a.fbar[1], &a.pbuf};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
     A.ai.clear();
@@ -570,6 +578,7 @@ void destroy_all(lbm_ctx* ctx) {
     invalidate_graphs(ctx);
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
+                          &I.lrec[0], &I.lrec[1],
                           &I.partial, &I.partial_scratch, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
                           &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc, &I.Acor};
         for (DevBuf* b : bufs) dfree(ctx, *b);
@@ -1302,6 +1311,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
         if ((rc = dalloc(ctx, a.rprec, sizeof(PRec) * n1 * (L + 1))) ||
             (rc = dalloc(ctx, a.rlcnt, sizeof(int) * (size_t)I.ntiles * (L + 1))) ||
             (rc = dalloc(ctx, a.rlent, sizeof(uint32_t) * (size_t)I.ntiles * LIST_CAP * (L + 1))) ||
+            (rc = dalloc(ctx, a.rlrec, (size_t)CAND_BYTES * I.ntiles * LIST_CAP * (L + 1))) ||
             (rc = dalloc(ctx, a.rgeo, sizeof(double) * NPV * n1 * (L + 1))) ||
             (rc = dalloc(ctx, a.rstate, sizeof(double) * 16 * n1 * (L + 1))) ||
             (rc = dalloc(ctx, a.fbar[0], sizeof(float) * (ctx->Q - 1) * (size_t)I.qstride)) ||
@@ -1324,10 +1334,12 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
             PRec* rp = P<PRec>(a.rprec);
             int* lc = P<int>(a.rlcnt);
             uint32_t* le = P<uint32_t>(a.rlent);
+            char* lr = P<char>(a.rlrec);
             if (k == L) {
                 d.prec_out = rp;
                 d.list_cnt[0] = lc;
                 d.list_ent[0] = le;
+                d.list_rec[0] = lr;
             } else {
                 const int par = k & 1;
                 d.f[par] = a.slot[k].ptr;
@@ -1338,6 +1350,8 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
                 d.list_ent[par] = le + (size_t)I.ntiles * LIST_CAP * k;
                 d.list_cnt[par ^ 1] = lc + (size_t)I.ntiles * (k + 1);
                 d.list_ent[par ^ 1] = le + (size_t)I.ntiles * LIST_CAP * (k + 1);
+                d.list_rec[par] = lr + (size_t)CAND_BYTES * I.ntiles * LIST_CAP * k;
+                d.list_rec[par ^ 1] = lr + (size_t)CAND_BYTES * I.ntiles * LIST_CAP * (k + 1);
                 d.adj_geo = P<double>(a.rgeo) + NPV * n1 * k;
                 d.rec_state = P<double>(a.rstate) + 16 * n1 * (k + 1);
                 if (sh.tma) {

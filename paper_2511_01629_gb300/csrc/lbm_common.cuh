@@ -108,15 +108,19 @@ template <> __device__ __forceinline__ __half to_store<__half>(float v, float s)
 }
 
 // -------------------------------------------------------- indicator test ---
-// Candidate particle of a tile, staged in shared memory.
-struct Cand {
+// Candidate particle of a tile, staged in shared memory.  The particle kernel
+// also writes these records into each tile's list (list_rec), 64 bytes each,
+// so that the TMA kernel can fetch a tile's candidates with one bulk copy.
+struct __align__(16) Cand {
     int ref[3];
     float frac[3];
     float R2lo, R2hi;
     float a[3];
     int p;  // particle index within the instance
     int k;  // partial slot of this tile in the particle's bounding box
+    int pad[3];
 };
+static_assert(sizeof(Cand) == CAND_BYTES, "candidate records are copied in 64-byte units");
 
 // Per-tile geometry and collision constants, copied out of the instance
 // descriptor into registers: the hot loops must not reload them after every
@@ -750,8 +754,14 @@ __device__ void finalize_rotation(const InstDesc& in, int p, const long long* v,
     }
 }
 
+// Where population q of node (x, y, z) pulls from (Eq. 10, left side): the
+// element of the previous post-collision buffer, and the term added to it.
+// Across a periodic face the source wraps; across a wall (the first wall axis
+// in the order x, y, z) the node's own opposite population bounces back, plus
+// the moving-wall term 2 w_q (c_q . u_w) / cs^2.
 template <int Q, class S>
-__device__ __noinline__ float pull_scalar(const InstDesc& in, const S* fin, int q, int x, int y, int z) {
+__device__ __forceinline__ const S* pull_source(const InstDesc& in, const S* fin, int q, int x, int y, int z,
+                                                float* add) {
     using L = Lat<Q>;
     const int c[3] = {L::c(q, 0), L::c(q, 1), L::c(q, 2)};
     int src[3] = {x - c[0], y - c[1], z - c[2]};
@@ -763,13 +773,20 @@ __device__ __noinline__ float pull_scalar(const InstDesc& in, const S* fin, int 
         }
     }
     if (axis >= 0) {
-        const int qo = L::opp(q);
+        *add = in.wterm[axis][face][q];
         const long long off = ((long long)z * in.n[1] + y) * in.pitch + x;
-        return VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (long long)(qo - 1) * in.qstride + off,
-                                                       in.s_load) + in.wterm[axis][face][q];
+        return fin + (long long)(L::opp(q) - 1) * in.qstride + off;
     }
+    *add = 0.f;
     const long long off = ((long long)src[2] * in.n[1] + src[1]) * in.pitch + src[0];
-    return VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (long long)(q - 1) * in.qstride + off, in.s_load);
+    return fin + (long long)(q - 1) * in.qstride + off;
+}
+
+template <int Q, class S>
+__device__ __noinline__ float pull_scalar(const InstDesc& in, const S* fin, int q, int x, int y, int z) {
+    float add;
+    const S* p = pull_source<Q, S>(in, fin, q, x, y, z, &add);
+    return VecIO<S, 1 + (sizeof(S) == 2)>::load1(p, in.s_load) + add;
 }
 
 }  // namespace lbmpen

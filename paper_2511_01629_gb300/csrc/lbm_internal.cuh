@@ -95,6 +95,7 @@ template <> struct Lat<19> {
 //   and under 2^63 for R <= MAX_RADIUS_3D = 40 in 3D; a 3D sphere of radius
 //   120 (7.2e6 nodes) could reach 2^68, so larger spheres are refused.
 constexpr int NPV = 16;
+constexpr int CAND_BYTES = 64;  // one candidate record of a tile list (Cand)
 constexpr int FXBITS = 40;
 constexpr double MAX_RADIUS = 120.0;     // largest disk radius (2D)
 constexpr double MAX_RADIUS_3D = 40.0;   // largest sphere radius (3D)
@@ -150,6 +151,7 @@ struct InstDesc {
                               //   while the adjoint recomputes a segment into per-step slots)
     int* list_cnt[2];         // [ntiles]
     uint32_t* list_ent[2];    // [ntiles][LIST_CAP]
+    void* list_rec[2];        // [ntiles][LIST_CAP] 64-byte candidate records (Cand), same slots
     long long* partial;       // [np][maxk][NPV], cleared by the finalize kernel
     long long* partial_scratch;  // same shape: sink of launches that do not advance the state
     // particle state (FP64), [np][3] unless noted

@@ -229,20 +229,39 @@ __device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, A
                      (float)in.pconst[PCONST_N * p + PC_GFAC]);
 }
 
-// List entries of particle p in the tiles of its bounding box (lanes share).
+// List entries of particle p in the tiles of its bounding box (lanes share),
+// from its record for the next step (prec_out[p]): the entry p << KBITS | k
+// and, in the same slot, the 64-byte candidate record the TMA kernel copies.
 __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int lpar, int lane,
                              int nl) {
     const int cnt[3] = {at[0].na + at[0].nb, at[1].na + at[1].nb, at[2].na + at[2].nb};
     const int nt = cnt[0] * cnt[1] * cnt[2];
+    if (lane >= nt) return;
+    const PRec& pr = in.prec_out[p];
+    Cand cd;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cd.ref[d] = pr.ref[d];
+        cd.frac[d] = pr.frac[d];
+        cd.a[d] = pr.a[d];
+        cd.pad[d] = 0;
+    }
+    cd.R2lo = pr.R2lo;
+    cd.R2hi = pr.R2hi;
+    cd.p = p;
+    Cand* rec = static_cast<Cand*>(in.list_rec[lpar]);
     for (int k = lane; k < nt && k < in.maxk; k += nl) {
         const int kx = k % cnt[0], ky = (k / cnt[0]) % cnt[1], kz = k / (cnt[0] * cnt[1]);
         const int tc[3] = {axis_tile(at[0], kx), axis_tile(at[1], ky), axis_tile(at[2], kz)};
         const int local = (tc[2] * in.ntile[1] + tc[1]) * in.ntile[0] + tc[0];
         const int pos = atomicAdd(&in.list_cnt[lpar][local], 1);
-        if (pos < LIST_CAP)
+        if (pos < LIST_CAP) {
             in.list_ent[lpar][(long long)local * LIST_CAP + pos] = ((uint32_t)p << KBITS) | (uint32_t)k;
-        else
+            cd.k = k;
+            rec[(long long)local * LIST_CAP + pos] = cd;
+        } else {
             atomicOr(in.status, ST_CAPACITY);
+        }
     }
 }
 
