@@ -192,7 +192,9 @@ int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
  * path without a stalled GPU.  The fluid kernel's waits keep their own 2 s
  * bound.  seconds in [0, 60]. */
 int lbm_set_particle_wait_limit(lbm_ctx* ctx, double seconds);
-/* Kernel launches issued by one lbm_step(ctx, 1) (fluid + particle kernels). */
+/* Kernel launches issued by one lbm_step(ctx, 1): the fluid kernel, then with
+ * particles the box sums of Eq. 22 and the particle kernel (one launch, or one
+ * per phase when its blocks cannot all be resident). */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 /* Fluid kernel alone, one launch, for timing: the same fused kernel and
  * work as the fluid part of lbm_step, on the current state of every

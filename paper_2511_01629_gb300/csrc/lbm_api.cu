@@ -32,6 +32,7 @@ cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int nto
                              long long wait_ns);
 cudaError_t launch_publish(const InstDesc* insts, const PartRef* refs, int ntotal, int D, int lpar,
                            const Shape& sh, cudaStream_t st);
+cudaError_t launch_box_sums(const InstDesc* insts, const PartRef* refs, int ntotal, int D, cudaStream_t st);
 int tma_tile_width(int Q);
 bool tma_rows_ok(int rows);
 int fluid_tma_blocks_per_sm(int Q, int fp16, const Shape& sh, int stages, int ninst);
@@ -69,10 +70,12 @@ struct Instance {
     int ntile[3] = {1, 1, 1};
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
-    DevBuf f[2], prec, lcnt[2], lent[2], lrec[2], partial, partial_scratch, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
+    DevBuf f[2], prec, lcnt[2], lent[2], lrec[2], ubox, ubox_scratch, boxinfo, btot, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
         Ubar, Xf, Acor;
     std::vector<double> hR;      // radii (validation)
     std::vector<double> hratio;  // density ratios (per-particle constants)
+    std::vector<int> hbox;       // per particle: first entry of its velocity box, H (pairs)
+    long long box_entries = 0;   // entries of all velocity boxes
 };
 
 // Adjoint recording of one instance: checkpoints of the forward pass and the
@@ -269,8 +272,10 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.list_ent[1] = P<uint32_t>(I.lent[1]);
     d.list_rec[0] = I.lrec[0].ptr;
     d.list_rec[1] = I.lrec[1].ptr;
-    d.partial = P<long long>(I.partial);
-    d.partial_scratch = P<long long>(I.partial_scratch);
+    d.ubox = P<float>(I.ubox);
+    d.ubox_scratch = P<float>(I.ubox_scratch);
+    d.boxinfo = P<int2>(I.boxinfo);
+    d.btot = P<long long>(I.btot);
     d.X = P<double>(I.X);
     d.U = P<double>(I.U);
     d.W = P<double>(I.W);
@@ -362,7 +367,7 @@ int republish(lbm_ctx* ctx) {
     for (auto& I : ctx->inst) {
         if (I.np == 0) continue;
         CK(cudaMemsetAsync(I.lcnt[ctx->par].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
-        CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
+        if (I.ubox.ptr) CK(cudaMemsetAsync(I.ubox.ptr, 0xff, I.ubox.bytes, ctx->st));  // every entry empty (NaN)
     }
     if (ctx->np_total > 0)
         CK(launch_publish(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
@@ -439,7 +444,7 @@ int build_tmaps(lbm_ctx* ctx) {
     return LBM_OK;
 }
 
-// Tile grid, tile -> instance table, tile lists and partial slots for a shape.
+// Tile grid, tile -> instance table and tile lists for a shape.
 int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
     Shape sh = sh_in;
     if (ctx->D == 2) sh.tz = 1;
@@ -466,11 +471,6 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
             if ((rc = dalloc(ctx, I.lrec[b], (size_t)CAND_BYTES * I.ntiles * LIST_CAP))) return rc;
             CK(cudaMemsetAsync(I.lcnt[b].ptr, 0, sizeof(int) * I.ntiles, ctx->st));
         }
-        const size_t pb = sizeof(long long) * (size_t)std::max(I.cap, 1) * I.maxk * NPV;
-        const size_t had = I.partial.bytes;
-        if ((rc = dalloc(ctx, I.partial, pb))) return rc;
-        if ((rc = dalloc(ctx, I.partial_scratch, pb))) return rc;
-        if (I.partial.bytes != had) CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
     }
     ctx->ntiles = tile0;
     int rc = dalloc(ctx, ctx->d_tile_inst, sizeof(uint16_t) * tab.size());
@@ -516,6 +516,7 @@ int enqueue_step(lbm_ctx* ctx, cudaStream_t st) {
     if (rc) return rc;
     if (ctx->np_total > 0) {
         const int K = ctx->inst[0].cfg.K;
+        CK(launch_box_sums(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, st));
         const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
         CK(launch_particles(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
                             K, ctx->par ^ 1, ctx->shape, P<GridBar>(ctx->d_gridbar), fused, st,
@@ -545,10 +546,11 @@ int read_status(lbm_ctx* ctx) {
     CK(cudaMemcpy(&st, ctx->d_status.ptr, sizeof(int), cudaMemcpyDeviceToHost));
     if (st == 0) return LBM_OK;
     ctx->failed = true;
+    // a wait that gave up leaves the step half done, so later errors are its consequences
+    if (st & ST_TIMEOUT) return set_err(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up%s");
     if (st & ST_DIVERGED) return set_err(ctx, LBM_ERR_DIVERGED, "the flow diverged (|u| >= 0.5 or non-finite)%s");
     if (st & ST_PARTICLE) return set_err(ctx, LBM_ERR_PARTICLE, "a particle centre crossed a wall%s");
     if (st & ST_DISPLACEMENT) return set_err(ctx, LBM_ERR_DIVERGED, "a particle moved faster than 0.5 per step%s");
-    if (st & ST_TIMEOUT) return set_err(ctx, LBM_ERR_TIMEOUT, "a bounded device wait gave up%s");
     return set_err(ctx, LBM_ERR_CAPACITY, "a tile overlaps more particles than its list holds%s");
 }
 
@@ -579,7 +581,7 @@ void destroy_all(lbm_ctx* ctx) {
     for (auto& I : ctx->inst) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
                           &I.lrec[0], &I.lrec[1],
-                          &I.partial, &I.partial_scratch, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
+                          &I.ubox, &I.ubox_scratch, &I.boxinfo, &I.btot, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
                           &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc, &I.Acor};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
@@ -607,9 +609,8 @@ int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
     if ((rc = dalloc(ctx, I.pconst, sizeof(double) * PCONST_N * c))) return rc;
     if ((rc = dalloc(ctx, I.invc, sizeof(double) * c))) return rc;
     if ((rc = dalloc(ctx, I.Xsf, sizeof(float) * 8 * c))) return rc;
-    if ((rc = dalloc(ctx, I.partial, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
-    if ((rc = dalloc(ctx, I.partial_scratch, sizeof(long long) * c * std::max(I.maxk, 1) * NPV))) return rc;
-    CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
+    if ((rc = dalloc(ctx, I.boxinfo, sizeof(int2) * c))) return rc;
+    if ((rc = dalloc(ctx, I.btot, sizeof(long long) * NPV * c))) return rc;
     return LBM_OK;
 }
 
@@ -787,6 +788,21 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
     CK(cudaMemcpyAsync(P<double>(I.R) + I.np, radius, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(P<double>(I.ratio) + I.np, ratio, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(P<int>(I.count) + I.np, 0, sizeof(int) * n, ctx->st));
+    // velocity boxes of the new particles: side 2H + 1, H = ceil(R) + 2, after the existing ones
+    for (int k = 0; k < n; ++k) {
+        const int H = (int)ceil(radius[k]) + 2, side = 2 * H + 1;
+        I.hbox.push_back((int)I.box_entries);
+        I.hbox.push_back(H);
+        I.box_entries += D == 2 ? (long long)side * side : (long long)side * side * side;
+    }
+    if (I.box_entries >= (1LL << 31)) return set_err(ctx, LBM_ERR_INVALID, "velocity boxes exceed 2^31 entries%s");
+    {
+        const size_t eb = (size_t)I.box_entries * (D == 2 ? 8 : 16);
+        if ((rc = dalloc(ctx, I.ubox, eb)) || (rc = dalloc(ctx, I.ubox_scratch, eb))) return rc;
+        CK(cudaMemsetAsync(I.ubox.ptr, 0xff, I.ubox.bytes, ctx->st));  // every entry empty (NaN)
+        CK(cudaMemcpyAsync(I.boxinfo.ptr, I.hbox.data(), sizeof(int) * I.hbox.size(), cudaMemcpyHostToDevice,
+                           ctx->st));
+    }
     CK(cudaStreamSynchronize(ctx->st));
     I.np += n;
     I.hR.insert(I.hR.end(), radius, radius + n);
@@ -1181,7 +1197,7 @@ int lbm_launches_per_step(const lbm_ctx* ctx) {
     if (!ctx) return 0;
     if (ctx->np_total == 0) return 1;
     const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
-    return 1 + (fused ? 1 : 1 + ctx->inst[0].cfg.K);
+    return 2 + (fused ? 1 : 1 + ctx->inst[0].cfg.K);  // fluid, box sums, particles
 }
 
 long long lbm_steps_done(const lbm_ctx* ctx) { return ctx ? ctx->steps : 0; }
@@ -1453,6 +1469,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
             else
                 CK(launch_fluid(ctx->Q, ctx->fp16, dk, P<uint16_t>(ctx->d_tile_inst), ctx->ntiles, par, sh, 1,
                                 sh.persistent, ctx->grid, P<int>(ctx->d_tile_ctr), st));
+            if (ctx->np_total > 0) CK(launch_box_sums(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, st));
             if (ctx->np_total > 0)
                 CK(launch_particles(dk, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, K, par ^ 1, sh,
                                     P<GridBar>(ctx->d_gridbar), fused, st, ctx->wait_ns));
@@ -1480,7 +1497,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* seed_particles, const float
             if (I.np)
                 CK(cudaMemcpyAsync(a.rstate.ptr, st, sizeof(double) * 16 * I.np, cudaMemcpyDeviceToDevice, ctx->st));
             CK(cudaMemsetAsync(a.rlcnt.ptr, 0, sizeof(int) * I.ntiles, ctx->st));
-            CK(cudaMemsetAsync(I.partial.ptr, 0, I.partial.bytes, ctx->st));
+            if (I.ubox.ptr) CK(cudaMemsetAsync(I.ubox.ptr, 0xff, I.ubox.bytes, ctx->st));
         }
         if (ctx->np_total > 0)
             CK(launch_publish(dR + (size_t)L * ni, P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, 0, sh, ctx->st));

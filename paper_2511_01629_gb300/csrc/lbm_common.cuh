@@ -116,9 +116,11 @@ struct __align__(16) Cand {
     float frac[3];
     float R2lo, R2hi;
     float a[3];
-    int p;  // particle index within the instance
-    int k;  // partial slot of this tile in the particle's bounding box
-    int pad[3];
+    int p;     // particle index within the instance
+    int k;     // index of this tile among the tiles of the particle's bounding box
+    int boff;  // first entry of the particle's velocity box
+    int bh;    // H of the box: side 2H + 1, centred on ref
+    int pad;
 };
 static_assert(sizeof(Cand) == CAND_BYTES, "candidate records are copied in 64-byte units");
 
@@ -365,6 +367,60 @@ __device__ __forceinline__ void collide_pair2(float2* f, const float2* u, const 
     }
 }
 
+// tau = 1 (keep = 0, 1/tau = 1): f*_q = feq_q + F_q + chi S_q formed as one
+// chain of fused multiply-adds, feq_q = A_q t + A_q (c.u) and the opposite
+// feq = A_q t - A_q (c.u), so that the only rounding at the scale of f* is the
+// last one (four before).  In the solid, where alpha = 1/tau keeps the
+// non-equilibrium stress from step to step, the rounding of every step
+// accumulates, so fewer roundings per step is a smaller error.  No constant
+// is folded (A_q stays exact), so no momentum bias enters.  P and trP: the
+// penalty's Pi_neq and its trace / 3 (PEN only).
+template <int Q, int q>
+__device__ __forceinline__ float2 pcc2(const float2* P) {  // c_q^T Pi c_q
+    using L = Lat<Q>;
+    constexpr int cx = L::c(q, 0), cy = L::c(q, 1), cz = L::c(q, 2);
+    float2 r = bc2(0.f);
+    bool first = true;
+    const int dia[3] = {cx, cy, cz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (!dia[d]) continue;
+        r = first ? P[d] : add2(r, P[d]);
+        first = false;
+    }
+    if (cx * cy) r = fma2(bc2(cx * cy > 0 ? 2.0f : -2.0f), P[3], r);
+    if (cx * cz) r = fma2(bc2(cx * cz > 0 ? 2.0f : -2.0f), P[4], r);
+    if (cy * cz) r = fma2(bc2(cy * cz > 0 ? 2.0f : -2.0f), P[5], r);
+    return r;
+}
+
+template <int Q, int q, bool PEN>
+__device__ __forceinline__ void collide_pair2_t1(float2* f, const float2* u, const float2* a, float2 base,
+                                                 float2 nua, const CollK& k, const float2* P, float2 trP,
+                                                 bool solid0, bool solid1) {
+    if constexpr (q < Q) {
+        if constexpr (pair_head<Q>(q)) {
+            using L = Lat<Q>;
+            constexpr int qo = L::opp(q);
+            constexpr int cls = (Q == 9 ? q >= 5 : q >= 7) ? 1 : 0;
+            const float2 cu = cdot2<Q, q>(u), ca = cdot2<Q, q>(a);
+            const float2 t = fma2(mul2(bc2(1.5f), cu), cu, base);
+            const float2 Fq = fma2(ca, fma2(bc2(3.0f), cu, bc2(1.0f)), nua);
+            const float2 Fo = fma2(ca, fma2(bc2(3.0f), cu, bc2(-1.0f)), nua);
+            float2 gq = mul2(bc2(k.fA[cls]), Fq), go = mul2(bc2(k.fA[cls]), Fo);
+            if constexpr (PEN) {  // opposite velocities share c c, so one penalty for both
+                const float2 pq = sub2(pcc2<Q, q>(P), trP);
+                const float2 sq = fma2(bc2(k.sA[cls]), pq, gq), so = fma2(bc2(k.sA[cls]), pq, go);
+                gq = make_float2(solid0 ? sq.x : gq.x, solid1 ? sq.y : gq.y);
+                go = make_float2(solid0 ? so.x : go.x, solid1 ? so.y : go.y);
+            }
+            f[q - 1] = fma2(bc2(k.A[cls]), cu, fma2(bc2(k.A[cls]), t, gq));
+            f[qo - 1] = fma2(bc2(-k.A[cls]), cu, fma2(bc2(k.A[cls]), t, go));
+        }
+        collide_pair2_t1<Q, q + 1, PEN>(f, u, a, base, nua, k, P, trP, solid0, solid1);
+    }
+}
+
 // Penalty source on solid nodes (Eq. 17) in two parts: the non-equilibrium
 // momentum flux Pi_neq = sum_q (f_q - feq_q) c_q c_q of the pre-collision
 // populations (xx yy zz xy xz yz), taken before the collision overwrites f,
@@ -497,7 +553,16 @@ __device__ __forceinline__ void collide2(float2* f, const float2* a, bool solid0
 #pragma unroll
     for (int d = 0; d < 3; ++d) u_out[d] = u[d];
     *p_out = p;
-    if (solid0 || solid1) {
+    if (k.keep == 0.f) {  // tau = 1: one rounding at the scale of f* (see collide_pair2_t1)
+        if (solid0 || solid1) {
+            float2 P[6];
+            pi_neq2<Q>(f, u, base, P);
+            const float2 trP = mul2(add2(add2(P[0], P[1]), P[2]), bc2(1.0f / 3.0f));
+            collide_pair2_t1<Q, 1, true>(f, u, a, base, nua, k, P, trP, solid0, solid1);
+        } else {
+            collide_pair2_t1<Q, 1, false>(f, u, a, base, nua, k, nullptr, bc2(0.f), false, false);
+        }
+    } else if (solid0 || solid1) {
         float2 P[6];
         pi_neq2<Q>(f, u, base, P);
         collide_pair2<Q, 1>(f, u, a, base, nua, k);
@@ -534,9 +599,23 @@ __device__ __forceinline__ long long to_fx(float u) {
     return __float2ll_rn(u * 1099511627776.0f);  // u * 2^40 is exact; round to nearest even
 }
 
-// Exact warp sum of a 64-bit integer of magnitude below 2^51: three 21-bit
-// limbs, each summed by one integer reduction (32 lanes keep every limb sum
-// below 2^26), recombined exactly.
+// The same round(u * 2^FXBITS) by two 32-bit conversions (the 64-bit one
+// issues at the FP64 rate on this GPU): x = u 2^40 is exact, t = trunc(x 2^-20)
+// fits in 20 bits, x - t 2^20 is exact (a multiple of ulp(x) below 2^20 in
+// magnitude, so at most 24 significant bits), and since t 2^20 is an even
+// integer, rne(x) = t 2^20 + rne(x - t 2^20), ties included.
+__device__ __forceinline__ long long to_fx32(float u) {
+    u = fminf(fmaxf(u, -0.49999997f), 0.49999997f);
+    const float x = u * 1099511627776.0f;                  // 2^40, exact
+    const int t = __float2int_rz(x * 9.5367431640625e-7f);  // 2^-20, exact scaling
+    const float rem = fmaf(-(float)t, 1048576.0f, x);      // exact
+    return (long long)t * 1048576LL + (long long)__float2int_rn(rem);
+}
+
+// Exact warp sum of 64-bit integers: three 21-bit limbs (the top one signed),
+// each summed by one integer reduction (32 lanes keep every limb sum below
+// 2^26 in magnitude), recombined modulo 2^64, which is exact whenever the
+// total fits in int64.
 __device__ __forceinline__ long long warp_sum_fx(long long v) {
     const unsigned l0 = (unsigned)(v & 0x1FFFFF);
     const unsigned l1 = (unsigned)((v >> 21) & 0x1FFFFF);
@@ -553,61 +632,21 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
     return v;
 }
 
-// Sums of Eq. 22 of one warp over the nodes (V per lane) owned by each
-// candidate, added with integer atomics straight into the particle's slot for
-// this tile (integer adds do not depend on their order; the finalize kernel
-// reads the slot and clears it for the next step).
-template <int D, int V>
-__device__ __forceinline__ void row_partials(const Geo& in, const Cand* cand, int ncand,
-                                             long long* partial, int maxk, const int* slot,
-                                             const float (*uv)[V], int xl, int y, int z, int lane) {
-    for (int c = 0; c < ncand; ++c) {
-        bool mine = false;
-#pragma unroll
-        for (int e = 0; e < V; ++e) mine |= slot[e] == c;
-        if (!__any_sync(0xffffffffu, mine)) continue;
-        const Cand& cd = cand[c];
-        int icnt = 0, id[3] = {0, 0, 0}, idd[6] = {0, 0, 0, 0, 0, 0};
-        long long su[3] = {0, 0, 0}, sl[3] = {0, 0, 0};
-        const int dy = wrap_int(y - cd.ref[1], in.n[1], in.per[1]);
-        const int dz = D == 3 ? wrap_int(z - cd.ref[2], in.n[2], in.per[2]) : 0;
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            if (slot[e] != c) continue;
-            const int dx = wrap_int(xl + e - cd.ref[0], in.n[0], in.per[0]);
-            long long ux[3] = {to_fx(uv[0][e]), to_fx(uv[1][e]), D == 3 ? to_fx(uv[2][e]) : 0};
-            icnt += 1;
-            id[0] += dx; id[1] += dy; id[2] += dz;
-            idd[0] += dx * dx; idd[1] += dy * dy; idd[2] += dz * dz;
-            idd[3] += dx * dy; idd[4] += dx * dz; idd[5] += dy * dz;
-            su[0] += ux[0]; su[1] += ux[1]; su[2] += ux[2];
-            sl[2] += (long long)dx * ux[1] - (long long)dy * ux[0];
-            if (D == 3) {
-                sl[0] += (long long)dy * ux[2] - (long long)dz * ux[1];
-                sl[1] += (long long)dz * ux[0] - (long long)dx * ux[2];
-            }
-        }
-        long long v[NPV];
-        v[0] = __reduce_add_sync(0xffffffffu, icnt);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v[1 + k] = (k < D) ? __reduce_add_sync(0xffffffffu, id[k]) : 0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const bool need = D == 3 || k == 0 || k == 1 || k == 3;
-            v[4 + k] = need ? __reduce_add_sync(0xffffffffu, idd[k]) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            v[10 + k] = (k < D) ? warp_sum_fx(su[k]) : 0;
-            v[13 + k] = (D == 3 || k == 2) ? warp_sum_fx(sl[k]) : 0;
-        }
-        if (lane == 0) {
-            unsigned long long* dst = reinterpret_cast<unsigned long long*>(
-                partial + ((long long)cd.p * maxk + cd.k) * NPV);
-#pragma unroll
-            for (int k = 0; k < NPV; ++k)
-                if (v[k] != 0) atomicAdd(dst + k, (unsigned long long)v[k]);
-        }
+// Velocity of a node owned by candidate cd into the particle's box: entry
+// (d + H) of the offset d = node - floor(X) (minimum image on periodic axes,
+// |d| <= R + 1 < H).  The particle kernel takes the sums of Eq. 22 from there.
+template <int D>
+__device__ __forceinline__ void box_store(float* ubox, const Geo& g, const Cand& cd, int x, int y, int z,
+                                          float ux, float uy, float uz) {
+    const int side = 2 * cd.bh + 1;
+    const int dx = wrap_int(x - cd.ref[0], g.n[0], g.per[0]) + cd.bh;
+    const int dy = wrap_int(y - cd.ref[1], g.n[1], g.per[1]) + cd.bh;
+    if (D == 2) {
+        reinterpret_cast<float2*>(ubox)[cd.boff + dy * side + dx] = make_float2(ux, uy);
+    } else {
+        const int dz = wrap_int(z - cd.ref[2], g.n[2], g.per[2]) + cd.bh;
+        reinterpret_cast<float4*>(ubox)[cd.boff + ((long long)dz * side + dy) * side + dx] =
+            make_float4(ux, uy, uz, 0.f);
     }
 }
 
@@ -624,7 +663,7 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 // Rigid-body projection of particle p (Eq. 22 with rho_s cancelled): the
-// tile partials are exact integers, summed exactly, then converted to FP64.
+// box sums are exact integers, summed exactly, then converted to FP64.
 // Moments about the integer reference floor(X) are shifted to the centre:
 //   sum r x u = sum d x u - phi x sum u,
 //   sum r r^T = sum d d^T - phi sum d^T - sum d phi^T + n phi phi^T.

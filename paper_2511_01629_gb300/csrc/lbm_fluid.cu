@@ -156,8 +156,7 @@ __device__ __forceinline__ void fluid_tile(const InstDesc& in, int local, int pa
     Cand* cand = reinterpret_cast<Cand*>(smem);
     const Geo geo = make_geo(in);
     const CollK ck = make_collk<Q>(make_collp(in));
-    long long* const partial = commit ? in.partial : in.partial_scratch;
-    const int maxk = in.maxk;
+    float* const ubox = commit ? in.ubox : in.ubox_scratch;
 
     const int ntx = in.ntile[0], nty = in.ntile[1];
     const int tx = local % ntx, rest = local / ntx;
@@ -195,6 +194,10 @@ __device__ __forceinline__ void fluid_tile(const InstDesc& in, int local, int pa
             cd.R2hi = pr.R2hi;
             cd.p = p;
             cd.k = (int)(e & (MAXK - 1));
+            const int2 bi = in.boxinfo[p];
+            cd.boff = bi.x;
+            cd.bh = bi.y;
+            cd.pad = 0;
             cand[c] = cd;
         }
         if (commit && tid == 0) in.list_cnt[par ^ 1][local] = 0;
@@ -257,7 +260,11 @@ __device__ __forceinline__ void fluid_tile(const InstDesc& in, int local, int pa
             for (int q = 0; q < QS; ++q)
                 VecIO<S, V>::store(fout + (long long)q * in.qstride + off, f[q], in.s_store);
         }
-        if (ncand > 0) row_partials<D, V>(geo, cand, ncand, partial, maxk, slot, uv, xl, y, z, lane);
+        if (ncand > 0) {  // the solid nodes' velocities into their particles' boxes (Eq. 22)
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (slot[e] >= 0) box_store<D>(ubox, geo, cand[slot[e]], xl + e, y, z, uv[0][e], uv[1][e], uv[2][e]);
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(in.status, ST_DIVERGED);
 }

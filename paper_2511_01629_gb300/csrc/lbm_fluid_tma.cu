@@ -15,8 +15,8 @@
 // tile touches no global memory.  The copies of a stage are counted by its
 // mbarrier; each consumer lane pulls two adjacent nodes' populations from
 // shared memory at x - c_x, collides them with packed FP32x2 arithmetic,
-// stores them to HBM with 8-byte coalesced stores, and reduces the
-// per-particle sums of Eq. 22.  Rows whose source lies beyond a y or z face
+// stores them to HBM with 8-byte coalesced stores, and stores the velocity
+// of each solid node into its particle's box for the sums of Eq. 22.  Rows whose source lies beyond a y or z face
 // gather those populations from HBM directly, as the register-path kernel
 // does.
 //
@@ -112,7 +112,7 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 // producer nor the consumers go to global memory for them in the tile loop.
 struct __align__(16) TInst {
     const void* f[2];          // population buffers
-    long long* partial[2];     // projection sums: [0] the state's, [1] scratch
+    float* ubox[2];            // velocity boxes: [0] the state's, [1] scratch
     const PRec* prec;
     int* status;
     int* lcnt[2];              // tile list counts per parity
@@ -134,8 +134,8 @@ __device__ __forceinline__ void make_tinst(TInst& t, const InstDesc& in) {
         t.lcnt[b] = in.list_cnt[b];
         t.lrec[b] = static_cast<const Cand*>(in.list_rec[b]);
     }
-    t.partial[0] = in.partial;
-    t.partial[1] = in.partial_scratch;
+    t.ubox[0] = in.ubox;
+    t.ubox[1] = in.ubox_scratch;
     t.prec = in.prec;
     t.status = in.status;
     t.qstride = in.qstride;
@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         const int nx = h.ti.n[0], ny = h.ti.n[1], nz = h.ti.n[2];
         const float sload = h.ti.sload;
         const CollK ck = make_collk<Q>(CollP{h.ti.keep, h.ti.fpref, h.ti.alpha});
+        float* const ubox = h.ti.ubox[commit ? 0 : 1];
         const int x0 = h.x0, y0 = h.y0, z0 = h.z0;
         const S* stage = reinterpret_cast<const S*>(smem + s * LY.stage);
         const int ex = h.ex, ecx = h.ecx;
@@ -616,12 +617,11 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                         }
                     }
                 }
-                if (act) {
-                    const int slot[2] = {v0 ? sl0 : -1, v1 ? sl1 : -1};
-                    const float uv[3][2] = {{u[0].x, u[0].y}, {u[1].x, u[1].y}, {D == 3 ? u[2].x : 0.f, D == 3 ? u[2].y : 0.f}};
-                    row_partials<D, 2>(geo, cand, ncand, h.ti.partial[commit ? 0 : 1], h.ti.maxk, slot, uv, x, y,
-                                       z, lane);
-                }
+                // the solid nodes' velocities into their particles' boxes (Eq. 22)
+                if (v0 && own0 >= 0)
+                    box_store<D>(ubox, geo, cand[sl0], x, y, z, u[0].x, u[1].x, D == 3 ? u[2].x : 0.f);
+                if (v1 && own1 >= 0)
+                    box_store<D>(ubox, geo, cand[sl1], x + 1, y, z, u[0].y, u[1].y, D == 3 ? u[2].y : 0.f);
             }
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(h.ti.status, ST_DIVERGED);

@@ -10,9 +10,12 @@
 //   tile lists   list_cnt[2][ntiles], list_ent[2][ntiles][cap]: for each
 //                tile the particles whose bounding box overlaps it, built by
 //                the particle kernel for the next step (no per-node mask);
-//   partials     partial[np][maxk][NPV] int64: per particle and per tile of its
-//                bounding box, the sums of Eq. 22 over that tile, exact in
-//                fixed point (velocities in units of 2^-FXBITS).
+//   velocity boxes  ubox: per particle a box of (2H + 1)^D entries, H =
+//                ceil(R) + 2, centred on floor(X): the fluid kernel stores the
+//                velocity of each node the particle owns there (float2 in 2D,
+//                float4 in 3D), the particle kernel sums the entries into the
+//                exact fixed-point totals of Eq. 22 and resets them to NaN,
+//                the mark of an empty entry.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -80,7 +83,7 @@ template <> struct Lat<19> {
 };
 
 // ------------------------------------------------------------- descriptors --
-// Values per (particle, tile) partial, all int64:
+// Totals of Eq. 22 per particle, all int64:
 //   0 count, 1-3 sum d, 4-9 sum d_i d_j (xx, yy, zz, xy, xz, yz),
 //   10-12 sum u, 13-15 sum d x u;  d = node - floor(X) (integer offsets),
 //   u in fixed point round(u * 2^FXBITS).  Integer sums are exact and do not
@@ -136,7 +139,7 @@ struct InstDesc {
     int ntile[3];             // tiles per axis
     int tile0;                // first global tile of this instance
     int np;                   // particles
-    int maxk;                 // partial slots per particle
+    int maxk;                 // most tiles a particle's bounding box may cover (list slot k)
     int part0;                // global index of particle 0 (batched arrays)
     float tau_inv, keep;      // 1/tau and 1 - 1/tau
     float fpref;              // 1 - 1/(2 tau)
@@ -152,8 +155,10 @@ struct InstDesc {
     int* list_cnt[2];         // [ntiles]
     uint32_t* list_ent[2];    // [ntiles][LIST_CAP]
     void* list_rec[2];        // [ntiles][LIST_CAP] 64-byte candidate records (Cand), same slots
-    long long* partial;       // [np][maxk][NPV], cleared by the finalize kernel
-    long long* partial_scratch;  // same shape: sink of launches that do not advance the state
+    float* ubox;              // velocity boxes of the particles (see above), NaN when empty
+    float* ubox_scratch;      // same shape: sink of launches that do not advance the state
+    int2* boxinfo;            // [np] box of particle p: first entry, H
+    long long* btot;          // [np][NPV] the box's totals of Eq. 22 (k_box_sums)
     // particle state (FP64), [np][3] unless noted
     double* X;
     double* U;                // U^{n-1} entering the step, U^n after it

@@ -244,11 +244,15 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
         cd.ref[d] = pr.ref[d];
         cd.frac[d] = pr.frac[d];
         cd.a[d] = pr.a[d];
-        cd.pad[d] = 0;
+
     }
     cd.R2lo = pr.R2lo;
     cd.R2hi = pr.R2hi;
     cd.p = p;
+    const int2 bi = in.boxinfo[p];
+    cd.boff = bi.x;
+    cd.bh = bi.y;
+    cd.pad = 0;
     Cand* rec = static_cast<Cand*>(in.list_rec[lpar]);
     for (int k = lane; k < nt && k < in.maxk; k += nl) {
         const int kx = k % cnt[0], ky = (k / cnt[0]) % cnt[1], kz = k / (cnt[0] * cnt[1]);
@@ -404,34 +408,110 @@ __device__ bool grid_sync(GridBar* gb, int* status, unsigned long long limit_ns)
     return __syncthreads_and(ok) != 0;
 }
 
-// Phase 0: the rigid-body projection (Eq. 22) of the block's 8 particles.
-// Warp t sums the exact integer slots of particle t (lanes over slots,
-// clearing them for the next step); one thread per particle does the FP64 part.
-__device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
-                               long long (*tot)[NPV]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gp = gp0 + warp;
-    if (warp < PB && gp < ntotal && refs[gp].inst >= 0) {
-        const int p = refs[gp].p;
-        const int nt = min(in.prec[p].ntiles, in.maxk);  // overflow is flagged at publish
-        long long v[NPV];
+// The totals of Eq. 22 of every particle from its velocity box, one block of
+// BS_THREADS per particle, launched between the fluid kernel and the particle
+// kernel: the threads take the box's entries (3D: only the rows that can reach
+// the sphere), turn every filled one (the nodes the particle owned in this
+// step's fluid kernel) into exact integer sums, and mark it empty again for
+// the next step.  The warps' totals are exact (integer reductions; 64-bit
+// sums by limbs) and so is their sum, so the totals do not depend on the order.
+constexpr int BS_THREADS = 256;
+constexpr int BS_PER = 8;  // entries of a thread in flight at a time
+
+template <int D>
+__device__ __forceinline__ void box_block_sums(const InstDesc& in, int p, long long (*red)[NPV]) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int2 bi = in.boxinfo[p];
+    const int H = bi.y, side = 2 * H + 1;
+    const int nent = D == 2 ? side * side : side * side * side;  // < 2^31 for R <= 40
+    const int hmax = (H - 1) * (H - 1);  // owned nodes have |d| <= R + 1 <= H - 1
+    int icnt = 0, id[3] = {0, 0, 0}, idd[6] = {0, 0, 0, 0, 0, 0};
+    long long su[3] = {0, 0, 0}, sl[3] = {0, 0, 0};
+    const float nanv = __int_as_float(0x7fffffff);
+    for (int e0 = 0; e0 < nent; e0 += BS_THREADS * BS_PER) {
+        float4 u[BS_PER];
+        int dd[BS_PER][3];
 #pragma unroll
-        for (int k = 0; k < NPV; ++k) v[k] = 0;
-        for (int s = lane; s < nt; s += 32) {
-            longlong2* src = reinterpret_cast<longlong2*>(in.partial + ((long long)p * in.maxk + s) * NPV);
-#pragma unroll
-            for (int k = 0; k < NPV / 2; ++k) {
-                const longlong2 a = __ldcg(src + k);
-                v[2 * k] += a.x;
-                v[2 * k + 1] += a.y;
+        for (int j = 0; j < BS_PER; ++j) {
+            const int e = e0 + tid + BS_THREADS * j;
+            const int dx = e % side - H, dy = (e / side) % side - H, dz = D == 3 ? e / (side * side) - H : 0;
+            dd[j][0] = dx;
+            dd[j][1] = dy;
+            dd[j][2] = dz;
+            u[j] = make_float4(nanv, nanv, nanv, 0.f);
+            if (e < nent && (D == 2 || dy * dy + dz * dz <= hmax)) {
+                if (D == 2) {
+                    const float2 t = __ldcg(reinterpret_cast<const float2*>(in.ubox) + bi.x + e);
+                    u[j].x = t.x;
+                    u[j].y = t.y;
+                } else {
+                    u[j] = __ldcg(reinterpret_cast<const float4*>(in.ubox) + bi.x + e);
+                }
             }
         }
 #pragma unroll
-        for (int k = 0; k < NPV; ++k) {
-            const long long w = warp_sum_ll(v[k]);
-            if (lane == 0) tot[warp][k] = w;
+        for (int j = 0; j < BS_PER; ++j) {
+            if (!(u[j].x == u[j].x)) continue;  // empty (NaN)
+            const int dx = dd[j][0], dy = dd[j][1], dz = dd[j][2];
+            const long long ux[3] = {to_fx32(u[j].x), to_fx32(u[j].y), D == 3 ? to_fx32(u[j].z) : 0};
+            icnt += 1;
+            id[0] += dx; id[1] += dy; id[2] += dz;
+            idd[0] += dx * dx; idd[1] += dy * dy; idd[2] += dz * dz;
+            idd[3] += dx * dy; idd[4] += dx * dz; idd[5] += dy * dz;
+            su[0] += ux[0]; su[1] += ux[1]; su[2] += ux[2];
+            sl[2] += (long long)dx * ux[1] - (long long)dy * ux[0];
+            if (D == 3) {
+                sl[0] += (long long)dy * ux[2] - (long long)dz * ux[1];
+                sl[1] += (long long)dz * ux[0] - (long long)dx * ux[2];
+            }
+            const long long e = bi.x + (long long)(e0 + tid + BS_THREADS * j);
+            if (D == 2) reinterpret_cast<float2*>(in.ubox)[e] = make_float2(nanv, nanv);
+            else reinterpret_cast<float4*>(in.ubox)[e] = make_float4(nanv, nanv, nanv, 0.f);
         }
     }
+    long long v[NPV];
+    v[0] = __reduce_add_sync(0xffffffffu, icnt);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[1 + k] = k < D ? (long long)__reduce_add_sync(0xffffffffu, id[k]) : 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool need = D == 3 || k == 0 || k == 1 || k == 3;
+        v[4 + k] = need ? (long long)__reduce_add_sync(0xffffffffu, idd[k]) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[10 + k] = k < D ? warp_sum_fx(su[k]) : 0;
+        v[13 + k] = (D == 3 || k == 2) ? warp_sum_fx(sl[k]) : 0;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NPV; ++k) red[warp][k] = v[k];
+}
+
+__global__ void __launch_bounds__(BS_THREADS) k_box_sums(const InstDesc* __restrict__ insts,
+                                                       const PartRef* __restrict__ refs, int D) {
+    __shared__ long long red[BS_THREADS / 32][NPV];
+    const PartRef r = refs[blockIdx.x];
+    if (r.inst < 0) return;  // padding entry (block-uniform)
+    const InstDesc& in = insts[r.inst];
+    if (D == 2) box_block_sums<2>(in, r.p, red);
+    else box_block_sums<3>(in, r.p, red);
+    __syncthreads();
+    if (threadIdx.x < NPV) {
+        long long t = 0;
+        for (int w = 0; w < BS_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        in.btot[(long long)r.p * NPV + threadIdx.x] = t;
+    }
+}
+
+// Phase 0: the rigid-body projection (Eq. 22) of the block's 8 particles from
+// their box totals; one thread per particle component does the FP64 part.
+__device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
+                               long long (*tot)[NPV]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gp = gp0 + warp;
+    if (warp < PB && lane < NPV && gp < ntotal && refs[gp].inst >= 0)
+        tot[warp][lane] = __ldcg(in.btot + (long long)refs[gp].p * NPV + lane);
     __syncthreads();
     // one lane per (particle, component): translation on warp 0, rotation on warp 1
     const int sl = lane & (PB - 1), c = lane / PB;
@@ -459,14 +539,6 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
     const bool mine = warp < PB && gp < ntotal && refs[gp].inst >= 0;
     const int i = mine ? refs[gp].p : 0;
     double f1[3] = {0, 0, 0}, f2[3] = {0, 0, 0};
-    if (src == 0 && mine) {  // the projection read this step's slots: clear them for the next
-        const int nt = min(in.prec[i].ntiles, in.maxk);
-        for (int s = lane; s < nt; s += 32) {
-            longlong2* dst = reinterpret_cast<longlong2*>(in.partial + ((long long)i * in.maxk + s) * NPV);
-#pragma unroll
-            for (int k = 0; k < NPV / 2; ++k) dst[k] = make_longlong2(0, 0);
-        }
-    }
     const float4* Xfb = reinterpret_cast<const float4*>(in.Xf) + (long long)src * in.np;
     const float4* Xsb = reinterpret_cast<const float4*>(in.Xsf) + (long long)src * in.np;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), xi2 = xi;
@@ -569,6 +641,11 @@ cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int nto
     }
     for (int ph = 0; ph <= K; ++ph)
         k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, ph, ph, lpar, sh, gb, lim);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_sums(const InstDesc* insts, const PartRef* refs, int ntotal, int D, cudaStream_t st) {
+    k_box_sums<<<ntotal, BS_THREADS, 0, st>>>(insts, refs, D);
     return cudaGetLastError();
 }
 

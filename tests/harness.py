@@ -82,3 +82,23 @@ def oracle_run(w, steps, parallel=True):
     out = ref.fields(), ref.particles()
     ref.close()
     return out
+
+
+def stored_fd():
+    """The stored central differences of the adjoint workload
+    (tests/golden/make_oracle_references.py): h, the first step at which the
+    +-h runs use different solid domains, and J(+h), J(-h) every 50 steps."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "adjoint_disk_seed0_fd.txt")
+    h, flips, rows = None, {}, {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        if f[0] == "h":
+            h = float(f[1])
+        elif f[0] == "flip":
+            flips[f[1]] = int(f[2])
+        else:
+            rows.setdefault(f[0], {})[int(f[1])] = (float(f[2]), float(f[3]))
+    return h, flips, rows

@@ -6,7 +6,7 @@ and the terminal velocity of a settling disk.
 Velocity errors are reported relative to U_ref = max |u_oracle| of the
 compared step, and in lattice units (the lattice speed c = 1).  Bounds:
 1e-6 of U_ref for FP32 and 1e-3 of U_ref for FP16 storage, and 0.5 % for the
-terminal velocity.  The errors come from rounding: every step rounds
+terminal velocity of a disk in a confined channel that does reach it.  The errors come from rounding: every step rounds
 populations of size ~U/3 (FP32: a random walk of ~1e-7 of U_ref per step;
 FP16: the 11-bit significand of IEEE half).
 """
@@ -105,36 +105,60 @@ def test_fp16_storage_many_disks_100_steps(many_case):
     assert cf["dp_f"] < 1e-3, cf
 
 
-TERMINAL = dict(seed=5, nx=80, ny=320, radius=6.0, ratio=1.5)
-T_STEPS, T_TAIL = 4000, 400
+# A disk settling in a confined channel (48 x 480 closed box, R = 6, ratio 1.5,
+# gravity 2e-5): the walls set the drag, the approach to terminal velocity
+# takes a few W^2 / (pi^2 nu) ~ 1400 steps, and the disk crosses a lattice
+# node every ~5000 steps, so means over 5000-step windows average the
+# discrete indicator's stepping.  (In the 400 x 1600 box of the single-disk
+# workload the approach takes ~W^2 / nu ~ 10^6 steps: not terminal at 20,000.)
+TERMINAL = dict(seed=1, nx=48, ny=480, radius=6.0, ratio=1.5)
+T_STEPS, T_EVERY, T_WIN = 20000, 100, 5000
+
+
+def _terminal_workload():
+    w = W.single_disk(**TERMINAL)
+    w.g_grav = (0.0, -2e-5, 0.0)
+    return w
 
 
 def _settling_series(step, read):
-    step(T_STEPS - T_TAIL)
     v = []
-    for _ in range(T_TAIL):
-        step(1)
+    for _ in range(T_STEPS // T_EVERY):
+        step(T_EVERY)
         v.append(read())
-    return float(np.mean(v))
+    return np.array(v)
 
 
 @pytest.fixture(scope="module")
 def oracle_terminal():
-    w = W.single_disk(**TERMINAL)
-    _, ref = make_pair(w)
-    return _settling_series(ref.step, lambda: ref.particles()["U"][0, 1])
+    import oracle
+    from harness import oracle_config
+    w = _terminal_workload()
+    ref = oracle.Sim(oracle_config(w), parallel=True)
+    ref.add_particles(w.pos, w.radius, w.ratio)
+    v = _settling_series(ref.step, lambda: ref.particles()["U"][0, 1])
+    ref.close()
+    return v
+
+
+def _window_means(v):
+    k = T_WIN // T_EVERY
+    return v[-k:].mean(), v[-2 * k:-k].mean()
 
 
 @gpu
 @pytest.mark.parametrize("storage", [lbm.LBM_FP32, lbm.LBM_FP16])
 def test_terminal_velocity_of_settling_disk(storage, oracle_terminal):
-    """Mean settling velocity over the last 10 % of 4000 steps (80 x 320 box,
-    R = 6, ratio 1.5, gravity 2e-6) within 0.5 % of the oracle's."""
-    w = W.single_disk(**TERMINAL)
+    """Terminal velocity, the mean settling velocity over the last 5000 of
+    20,000 steps, within 0.5 % of the oracle's; the oracle's mean over the
+    5000 steps before differs by less than 0.1 %, so the disk is terminal."""
+    w = _terminal_workload()
     sim, _ = make_pair(w, storage=storage, graphs=16)
-    Vg = _settling_series(sim.step, lambda: sim.particles()["U"][0, 1])
+    vg = _settling_series(sim.step, lambda: sim.particles()["U"][0, 1])
     sim.close()
-    Vo = oracle_terminal
-    print("terminal velocity", storage, Vg, Vo)
+    Vo, Vo_prev = _window_means(oracle_terminal)
+    Vg, _ = _window_means(vg)
+    print("terminal velocity", storage, Vg, Vo, "oracle previous window", Vo_prev)
     assert Vo < 0.0
+    assert abs(Vo - Vo_prev) < 1e-3 * abs(Vo), (Vo, Vo_prev)
     assert abs(Vg - Vo) <= 0.005 * abs(Vo), (Vg, Vo)

@@ -260,3 +260,32 @@ def test_autograd_function_matches_twin():
         _close(ratio.grad[b].numpy(), r.grad.numpy(), what="ratio")
         _close(X0.grad[b].numpy(), x.grad[:, :2].numpy(), what="X0")
         _close(U0.grad[b].numpy(), u.grad[:, :2].numpy(), what="U0")
+
+
+@gpu
+@pytest.mark.parametrize("param", ["ratio", "alpha", "x0", "y0"])
+def test_adjoint_at_bench_geometry_matches_oracle_fd(param):
+    """The benched adjoint workload at full size (400 x 1600, R = 12, ratio 1.5,
+    alpha = 1/tau, J = final height) over the longest stored window in which
+    the oracle's +-h runs keep the same solid domains: dJ/d(ratio, alpha,
+    initial x, initial y) from the GPU adjoint against the oracle's central
+    differences (h = 1e-4) at <= 1e-4 relative.  Along x the frozen
+    indicator makes both exactly zero."""
+    from paper_2511_01629_gb300 import workloads as W
+    from harness import stored_fd
+    h, flips, rows = stored_fd()
+    n = max(k for k in rows[param] if k < flips[param])
+    jp, jm = rows[param][n]
+    fd = (jp - jm) / (2 * h)
+    w = W.adjoint_disk(0, steps=n)
+    sim = lbm.from_workloads([w])
+    sim.set_graphs(16)
+    sim.adjoint_forward(n, 0)
+    g = sim.adjoint_backward([{"X": np.array([[0.0, 1.0]])}])[0]
+    sim.close()
+    adj = {"ratio": g["ratio"][0], "alpha": g["alpha"], "x0": g["X"][0, 0], "y0": g["X"][0, 1]}[param]
+    print("adjoint vs FD", param, n, adj, fd)
+    if param == "x0":
+        assert fd == 0.0 and adj == 0.0, (adj, fd)
+    else:
+        assert abs(adj - fd) <= 1e-4 * abs(fd), (adj, fd)
