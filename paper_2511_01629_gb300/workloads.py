@@ -185,6 +185,40 @@ def adjoint_disk(seed: int = 0, nx: int = 400, ny: int = 1600, steps: int = 5000
     return w
 
 
+def couette_migration(H: int = 200, diameter: float = 50.0, length_d: float = 100.0,
+                       U_w: float = 1.0 / 60.0, steps: int = 700000) -> Workload:
+    """Lateral migration of a neutrally buoyant disk in plane Couette flow
+    (Sec. 3.1): walls at y = -1/2 and H - 1/2 moving at -U_w/2 and +U_w/2,
+    periodic in x over L = length_d * D, tau = 1, rho_s = rho_f, the disk
+    released at x0 = 15 D and a distance D above the lower wall, the fluid at
+    rest at t = 0.  The paper's run: H = 200 = 4 D, L = 100 D, U_w = 1/60,
+    700,000 steps (shear time gamma t = 58)."""
+    L = int(round(length_d * diameter))
+    wall = [[[0.0] * 3 for _ in range(2)] for _ in range(3)]
+    wall[1][0][0], wall[1][1][0] = -0.5 * U_w, 0.5 * U_w
+    return Workload("couette_migration", 2, (L, H, 1), (1, 0, 1), tau=1.0, alpha=1.0,
+                    wall_u=wall, pos=[[15.0 * diameter, -0.5 + diameter]],
+                    radius=[0.5 * diameter], ratio=[1.0], steps=steps)
+
+
+def dkt(L: int = 200, g: float = 0.05, offset: float = 0.1, steps: int = 12000) -> Workload:
+    """Drafting, kissing and tumbling of two disks (Sec. 3.4) in lattice
+    units: a closed channel L x 4L with L = 10 D, two disks of diameter
+    D = L / 10 and density 1.01 rho_f on the centre line, 0.9 H and 0.85 H
+    above the lower wall (7.2 and 6.8 of 8), tau = 1, eps_p = eps_w = 2,
+    delta = 1.  Gravity 0.05 sets a settling velocity near 0.09 lattice units
+    (Re = D U / nu ~ 11).  The upper disk starts `offset` lattice units off the
+    centre line: two exactly centred disks keep the mirror symmetry and fall
+    as one kissing pair without tumbling."""
+    H = 4 * L
+    xc = 0.5 * (L - 1)
+    R = 0.05 * L
+    return Workload("dkt", 2, (L, H, 1), (0, 0, 1), tau=1.0, alpha=1.0, g_grav=(0.0, -g, 0.0),
+                    delta=1.0, eps_p=2.0, eps_w=2.0,
+                    pos=[[xc + offset, -0.5 + 0.9 * H], [xc, -0.5 + 0.85 * H]], radius=[R, R],
+                    ratio=[1.01, 1.01], steps=steps)
+
+
 def random_small(seed: int, D: int = 2, n=(24, 20, 1), periodic=(1, 0, 1), nparticles: int = 3,
                  rlo: float = 2.5, rhi: float = 5.0, tau: float = 0.9, alpha: Optional[float] = None,
                  g_grav=(0.0, -1e-4, 0.0), g_drive=(0.0, 0.0, 0.0)) -> Workload:

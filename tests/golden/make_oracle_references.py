@@ -19,7 +19,21 @@ GPU test suite (a 400 x 1600 oracle step takes ~30 ms on 8 cores):
       Up to that step (J(+h) - J(-h)) / 2h is the derivative of the
       recorded sequence of solid domains, which the discrete adjoint computes.
 
-  python tests/golden/make_oracle_references.py [trajectory|fd|all]
+  couette_migration_h40.txt
+      Lateral migration of a neutrally buoyant disk in plane Couette flow
+      (Sec. 3.1) at a fifth of the paper's size with the same particle and
+      channel Reynolds numbers: H = 40 = 4 D, L = 20 D, walls at -+U_w/2 with
+      U_w = 1/12 (gamma D^2 / nu = 1.25, U_w H / nu = 20), the disk released
+      a distance D above the lower wall, 28,000 steps (gamma t = 58.3, the
+      paper's shear time): every 200 steps the step count, X, Y, U_x, U_y,
+      omega and the node count.
+
+  dkt_l200.txt
+      Drafting, kissing and tumbling of two disks (Sec. 3.4; workloads.dkt):
+      200 x 800 closed channel, D = 20, ratio 1.01, 12,000 steps: every 100
+      steps the step count and, per disk, X, Y, U_x, U_y, omega, count.
+
+  python tests/golden/make_oracle_references.py [trajectory|fd|couette|dkt|all]
 """
 import hashlib
 import os
@@ -35,6 +49,8 @@ import oracle  # noqa: E402
 from paper_2511_01629_gb300 import workloads as W  # noqa: E402
 
 TRAJ = os.path.join(HERE, "single_disk_seed0_trajectory.txt")
+COUETTE = os.path.join(HERE, "couette_migration_h40.txt")
+DKT = os.path.join(HERE, "dkt_l200.txt")
 FD = os.path.join(HERE, "adjoint_disk_seed0_fd.txt")
 EVERY = 50
 
@@ -114,6 +130,51 @@ def finite_differences(steps=5000, h=1e-4):
                 fh.write("%s %d %.17g %.17g\n" % (name, n, jp, jm))
 
 
+def couette_case():
+    """The reduced Couette migration case of couette_migration_h40.txt."""
+    return W.couette_migration(H=40, diameter=10.0, length_d=20.0, U_w=1.0 / 12.0, steps=28000)
+
+
+def _particle_rows(w, every, header):
+    s = oracle.Sim(_config(w), parallel=True)
+    s.add_particles(w.pos, w.radius, w.ratio)
+    rows = []
+    for n in range(0, w.steps + 1, every):
+        if n:
+            s.step(every)
+        p = s.particles()
+        row = [n]
+        for i in range(w.num_particles):
+            row += [*p["X"][i, :2], *p["U"][i, :2], p["W"][i, 2], p["count"][i]]
+        rows.append(row)
+    s.close()
+    return "".join(header) + "".join(
+        " ".join(["%d" % r[0]] + ["%d" % v if (k % 6) == 5 else "%.17g" % v for k, v in enumerate(r[1:])])
+        + "\n" for r in rows)
+
+
+def couette():
+    w = couette_case()
+    text = _particle_rows(w, 200, [
+        "# couette_migration H = 40, D = 10, L = 20 D, U_w = 1/12 (walls at -+U_w/2), tau = 1,\n",
+        "# rho_s = rho_f, disk released at (15 D, D - 1/2); FP64 oracle\n",
+        "# (tests/golden/make_oracle_references.py); fluid at rest at step 0.\n",
+        "# step X Y U_x U_y omega count\n"])
+    with open(COUETTE, "w") as fh:
+        fh.write(text)
+
+
+def dkt():
+    w = W.dkt()
+    text = _particle_rows(w, 100, [
+        "# dkt: 200 x 800 closed channel, two disks R = 10, ratio 1.01, gravity 0.05, tau = 1,\n",
+        "# eps_p = eps_w = 2, delta = 1; disk 0 starts above disk 1 (workloads.dkt); FP64 oracle\n",
+        "# (tests/golden/make_oracle_references.py).\n",
+        "# step then per disk: X Y U_x U_y omega count\n"])
+    with open(DKT, "w") as fh:
+        fh.write(text)
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "all"
     oracle.build(parallel=True)
@@ -121,3 +182,7 @@ if __name__ == "__main__":
         trajectory()
     if what in ("fd", "all"):
         finite_differences()
+    if what in ("couette", "all"):
+        couette()
+    if what in ("dkt", "all"):
+        dkt()
