@@ -80,6 +80,10 @@ def lib(parallel: bool = False):
         L.orc_create.restype = C.c_void_p
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_add_particles.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_void_p, C.c_void_p]
+        L.orc_add_ellipses.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_void_p,
+                                       C.c_void_p]
+        L.orc_collision_forces_ellipse.argtypes = [C.POINTER(Config), C.c_int, _dp, _dp, _dp, _dp,
+                                                   _dp, _dp]
         L.orc_set_f.argtypes = [C.c_void_p, _dp]
         L.orc_get_f.argtypes = [C.c_void_p, _dp]
         L.orc_set_static_solid.argtypes = [C.c_void_p, C.c_void_p]
@@ -180,6 +184,19 @@ def collision_forces(cfg: Config, X, R, ratio):
     return F
 
 
+def collision_forces_ellipse(cfg: Config, X, a, b, theta, ratio):
+    """Eqs. 19-21 for ellipses (2D): semi-axes a, b, orientation theta."""
+    n = len(a)
+    X3 = np.zeros((n, 3))
+    X = np.asarray(X, np.float64).reshape(n, -1)
+    X3[:, : X.shape[1]] = X
+    F = np.zeros((n, 3))
+    f64 = lambda v: np.ascontiguousarray(v, np.float64)
+    lib().orc_collision_forces_ellipse(C.byref(cfg), n, np.ascontiguousarray(X3), f64(a), f64(b),
+                                       f64(theta), f64(ratio), F)
+    return F
+
+
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
@@ -224,6 +241,19 @@ class Sim:
         vel = None if vel is None else np.ascontiguousarray(vel, np.float64).ravel()
         omega = None if omega is None else np.ascontiguousarray(omega, np.float64).ravel()
         self._L.orc_add_particles(self._h, len(R), pos, R, ratio, _ptr(vel), _ptr(omega))
+        self._keep = (vel, omega)
+
+    def add_ellipses(self, pos, a, b, theta, ratio, vel=None, omega=None):
+        """Ellipses (2D, Sec. 3.3): semi-axes a >= b > 0 and orientation theta
+        (angle of the a axis from +x)."""
+        f64 = lambda v: np.ascontiguousarray(v, np.float64).ravel()
+        vel = None if vel is None else f64(vel)
+        omega = None if omega is None else f64(omega)
+        a = f64(a)
+        rc = self._L.orc_add_ellipses(self._h, len(a), f64(pos), a, f64(b), f64(theta), f64(ratio),
+                                      _ptr(vel), _ptr(omega))
+        if rc != 0:
+            raise ValueError("oracle: ellipses need D = 2 and 0 < b <= a")
         self._keep = (vel, omega)
 
     @property

@@ -152,7 +152,9 @@ struct orc_sim {
     double* a;      /* acceleration f/rho [N][3] */
     int np, cap;
     double *X, *U, *W, *theta, *A; /* [cap][3] */
-    double *R, *ratio;             /* [cap] */
+    double *R, *ratio;             /* [cap]; R = semi-major axis a of an ellipse */
+    double* b;                     /* [cap] semi-minor axis; b == R for a disk */
+    double *ec, *es;               /* [cap] cos, sin of the orientation theta^n (2D) */
     long* count;                   /* [cap] solid nodes at the last step */
     long steps;
 };
@@ -174,10 +176,25 @@ static double disp(const orc_config* c, int d, double xnode, double Xp) {
     return dx;
 }
 
+static int is_ellipse(const orc_sim* s, int p) { return s->b[p] != s->R[p]; }
+
 /* Eq. 9 on the lattice: node x is in Omega_s,p iff |x - X_p|^2 <= R_p^2, the
    squared distance summed axis by axis in order x, y, z with separate
-   roundings; overlapping particles give the node to the lowest index. */
+   roundings; overlapping particles give the node to the lowest index.
+   Ellipse (Sec. 3.3, 2D only): semi-axes a = R_p along the orientation
+   e = (cos theta, sin theta) and b_p along e_perp = (-sin theta, cos theta);
+   with u = r . e and v = r . e_perp (r = x - X_p, minimum image) the node is
+   inside iff b^2 u^2 + a^2 v^2 <= a^2 b^2, i.e. (u/a)^2 + (v/b)^2 <= 1
+   without a division, each product and sum rounded separately. */
 static int node_inside(const orc_sim* s, int p, const int* xyz) {
+    if (is_ellipse(s, p)) {
+        double dx = disp(&s->c, 0, (double)xyz[0], s->X[3 * p + 0]);
+        double dy = disp(&s->c, 1, (double)xyz[1], s->X[3 * p + 1]);
+        double u = dx * s->ec[p] + dy * s->es[p];
+        double v = dy * s->ec[p] - dx * s->es[p];
+        double a2 = s->R[p] * s->R[p], b2 = s->b[p] * s->b[p];
+        return b2 * (u * u) + a2 * (v * v) <= a2 * b2;
+    }
     double d2 = 0.0;
     for (int d = 0; d < s->c.D; ++d) {
         double dx = disp(&s->c, d, (double)xyz[d], s->X[3 * p + d]);
@@ -189,10 +206,16 @@ static int node_inside(const orc_sim* s, int p, const int* xyz) {
 /* Particles are visited in index order and a node keeps the first particle
    that contains it, so the lowest index wins.  Only the nodes of each
    particle's bounding box [X - R - 1, X + R + 1] (wrapped on periodic axes)
-   are tested; every node outside it is farther than R from the centre. */
+   are tested; every node outside it is farther than R from the centre (an
+   ellipse lies inside the circle of radius a = R).  The orientation of an
+   ellipse is theta^n, the z component of theta in 2D. */
 static void build_owner(orc_sim* s) {
     int D = s->c.D;
     for (long x = 0; x < s->N; ++x) s->owner[x] = -1;
+    for (int p = 0; p < s->np; ++p) {
+        s->ec[p] = cos(s->theta[3 * p + 2]);
+        s->es[p] = sin(s->theta[3 * p + 2]);
+    }
     for (int p = 0; p < s->np; ++p) {
         int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
         for (int d = 0; d < 3; ++d) {
@@ -246,7 +269,7 @@ void orc_destroy(orc_sim* s) {
     if (!s) return;
     free(s->f); free(s->fs); free(s->owner); free(s->mask); free(s->u); free(s->a);
     free(s->X); free(s->U); free(s->W); free(s->theta); free(s->A);
-    free(s->R); free(s->ratio); free(s->count);
+    free(s->R); free(s->ratio); free(s->count); free(s->b); free(s->ec); free(s->es);
     free(s);
 }
 
@@ -263,6 +286,9 @@ int orc_add_particles(orc_sim* s, int n, const double* pos, const double* R, con
         s->R = (double*)realloc(s->R, sizeof(double) * cap);
         s->ratio = (double*)realloc(s->ratio, sizeof(double) * cap);
         s->count = (long*)realloc(s->count, sizeof(long) * cap);
+        s->b = (double*)realloc(s->b, sizeof(double) * cap);
+        s->ec = (double*)realloc(s->ec, sizeof(double) * cap);
+        s->es = (double*)realloc(s->es, sizeof(double) * cap);
         s->cap = cap;
     }
     for (int i = 0; i < n; ++i) {
@@ -281,10 +307,31 @@ int orc_add_particles(orc_sim* s, int n, const double* pos, const double* R, con
                 for (int d = 0; d < 3; ++d) s->W[3 * p + d] = omega[3 * i + d];
         }
         s->R[p] = R[i];
+        s->b[p] = R[i];
+        s->ec[p] = 1.0;
+        s->es[p] = 0.0;
         s->ratio[p] = ratio[i];
         s->count[p] = 0;
     }
     s->np += n;
+    return 0;
+}
+
+/* Ellipses (2D): semi-axes a >= b > 0, orientation theta (angle of the a axis
+   from +x, counter-clockwise).  b == a gives a disk.  Returns -1 in 3D or for
+   bad axes. */
+int orc_add_ellipses(orc_sim* s, int n, const double* pos, const double* a, const double* b,
+                     const double* theta, const double* ratio, const double* vel,
+                     const double* omega) {
+    if (s->c.D != 2) return -1;
+    for (int i = 0; i < n; ++i)
+        if (!(b[i] > 0.0 && b[i] <= a[i])) return -1;
+    int first = s->np;
+    orc_add_particles(s, n, pos, a, ratio, vel, omega);
+    for (int i = 0; i < n; ++i) {
+        s->b[first + i] = b[i];
+        s->theta[3 * (first + i) + 2] = theta ? theta[i] : 0.0;
+    }
     return 0;
 }
 
@@ -426,10 +473,27 @@ void orc_rigid_projection(orc_sim* s, const double* u, double* U, double* W, lon
     projection(s, u, U, W, count);
 }
 
+/* Extent of particle p along the unit vector (nx, ny): R for a disk; for an
+   ellipse its support distance sqrt(a^2 (n.e)^2 + b^2 (n.e_perp)^2), the
+   distance from the centre to the tangent line normal to n. */
+static double extent(const double* R, const double* b, const double* ec, const double* es, int p,
+                     double nx, double ny) {
+    if (!b || b[p] == R[p]) return R[p];
+    double ne = nx * ec[p] + ny * es[p];
+    double np_ = ny * ec[p] - nx * es[p];
+    return sqrt(R[p] * R[p] * (ne * ne) + b[p] * b[p] * (np_ * np_));
+}
+
 /* Eqs. 19-21.  C = (rho_s - rho_f) |g| of the particle receiving the force;
-   the image of particle i behind wall k is its mirror across the wall plane. */
-void orc_collision_forces(const orc_config* cfg, int np, const double* X, const double* R,
-                          const double* ratio, double* F) {
+   the image of particle i behind wall k is its mirror across the wall plane.
+   Ellipses (the paper states the forces for disks only): R_i + R_j becomes
+   the sum of the two extents along the line of centres, and 2 R_i of a wall
+   twice the extent along the wall normal, so that the forces act when the
+   gap between the two shapes, measured along that line, is below delta (for
+   walls delta / 2, as for disks).  b, ec, es = NULL: all disks. */
+static void collision_forces(const orc_config* cfg, int np, const double* X, const double* R,
+                             const double* b, const double* ec, const double* es,
+                             const double* ratio, double* F) {
     double gmag = sqrt(dot3(cfg->g_grav, cfg->g_grav));
     int D = cfg->D;
     for (int i = 0; i < np; ++i) {
@@ -450,6 +514,9 @@ void orc_collision_forces(const orc_config* cfg, int np, const double* X, const 
             }
             double dij = sqrt(dot3(dv, dv));
             double range = R[i] + R[j] + cfg->delta;
+            if (b && (b[i] != R[i] || b[j] != R[j]) && dij > 0.0)
+                range = extent(R, b, ec, es, i, dv[0] / dij, dv[1] / dij) +
+                        extent(R, b, ec, es, j, dv[0] / dij, dv[1] / dij) + cfg->delta;
             if (dij <= range) {
                 double s = (range - dij) / cfg->delta;
                 for (int d = 0; d < 3; ++d) Fi[d] += C / cfg->eps_p * dv[d] * s * s;
@@ -462,7 +529,8 @@ void orc_collision_forces(const orc_config* cfg, int np, const double* X, const 
                 double Xim = 2.0 * walls[face] - X[3 * i + d]; /* mirror image */
                 double diff = X[3 * i + d] - Xim;
                 double dprime = fabs(diff);
-                double range = 2.0 * R[i] + cfg->delta;
+                double range = 2.0 * extent(R, b, ec, es, i, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0) +
+                               cfg->delta;
                 if (dprime <= range) {
                     double s = (range - dprime) / cfg->delta;
                     Fi[d] += C / cfg->eps_w * diff * s * s;
@@ -471,6 +539,25 @@ void orc_collision_forces(const orc_config* cfg, int np, const double* X, const 
         }
         for (int d = 0; d < 3; ++d) F[3 * i + d] = Fi[d];
     }
+}
+
+void orc_collision_forces(const orc_config* cfg, int np, const double* X, const double* R,
+                          const double* ratio, double* F) {
+    collision_forces(cfg, np, X, R, NULL, NULL, NULL, ratio, F);
+}
+
+void orc_collision_forces_ellipse(const orc_config* cfg, int np, const double* X, const double* a,
+                                  const double* b, const double* theta, const double* ratio,
+                                  double* F) {
+    double* ec = (double*)malloc(sizeof(double) * (np > 0 ? np : 1));
+    double* es = (double*)malloc(sizeof(double) * (np > 0 ? np : 1));
+    for (int i = 0; i < np; ++i) {
+        ec[i] = cos(theta[i]);
+        es[i] = sin(theta[i]);
+    }
+    collision_forces(cfg, np, X, a, b, ec, es, ratio, F);
+    free(ec);
+    free(es);
 }
 
 /* Algorithm 1 (dt = 1) for all particles together, since F_col at each
@@ -497,9 +584,9 @@ static int particle_update(orc_sim* s, const double* Un, const double* Wn) {
     double* corr = (double*)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
     double h = 1.0 / K;
     for (int k = 1; k <= K; ++k) {
-        orc_collision_forces(&s->c, np, Xk, s->R, s->ratio, F1);
+        collision_forces(&s->c, np, Xk, s->R, s->b, s->ec, s->es, s->ratio, F1);
         for (int i = 0; i < 3 * np; ++i) Xs[i] = Xk[i] + h * Ubar[i];
-        orc_collision_forces(&s->c, np, Xs, s->R, s->ratio, F2);
+        collision_forces(&s->c, np, Xs, s->R, s->b, s->ec, s->es, s->ratio, F2);
         for (int p = 0; p < np; ++p) {
             double M = s->ratio[p] * s->c.rho_f * (double)s->count[p];
             for (int d = 0; d < 3; ++d) {

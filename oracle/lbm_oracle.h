@@ -53,12 +53,20 @@ void orc_source(int D, double alpha, const double* f, const double* feq, double*
 /* collision force on every particle at positions X (np*3), Eqs. 19-21 */
 void orc_collision_forces(const orc_config* cfg, int np, const double* X, const double* R,
                           const double* ratio, double* F);
+/* the same for ellipses (2D): semi-axes a, b, orientation theta (np each) */
+void orc_collision_forces_ellipse(const orc_config* cfg, int np, const double* X, const double* a,
+                                  const double* b, const double* theta, const double* ratio,
+                                  double* F);
 
 /* simulation */
 orc_sim* orc_create(const orc_config* cfg);
 void     orc_destroy(orc_sim* s);
 int      orc_add_particles(orc_sim* s, int n, const double* pos, const double* R,
                            const double* ratio, const double* vel, const double* omega);
+/* ellipses (2D, Sec. 3.3): semi-axes a >= b > 0, orientation theta (nullable) */
+int      orc_add_ellipses(orc_sim* s, int n, const double* pos, const double* a, const double* b,
+                          const double* theta, const double* ratio, const double* vel,
+                          const double* omega);
 void     orc_set_f(orc_sim* s, const double* f);   /* post-collision state [Q][N] */
 void     orc_get_f(const orc_sim* s, double* f);
 void     orc_set_static_solid(orc_sim* s, const int* mask); /* test hook, NULL clears */

@@ -76,6 +76,10 @@ class Workload:
     radius: List[float] = field(default_factory=list)
     ratio: List[float] = field(default_factory=list)
     steps: int = 0
+    # ellipses (2D): semi-minor axis and orientation per particle (radius is
+    # the semi-major axis); None = disks
+    minor: Optional[List[float]] = None
+    theta: Optional[List[float]] = None
 
     @property
     def nodes(self) -> int:
@@ -217,6 +221,22 @@ def dkt(L: int = 200, g: float = 0.05, offset: float = 0.1, steps: int = 12000) 
                     delta=1.0, eps_p=2.0, eps_w=2.0,
                     pos=[[xc + offset, -0.5 + 0.9 * H], [xc, -0.5 + 0.85 * H]], radius=[R, R],
                     ratio=[1.01, 1.01], steps=steps)
+
+
+def ellipse_settling(L: int = 200, g: float = 2.178e-3, theta0: float = math.pi / 4,
+                     steps: int = 30000) -> Workload:
+    """A single ellipse settling in a vertical channel (Sec. 3.3) in lattice
+    units: semi-axes a = L / 8 and b = a / 2, channel L x 10 L with walls on
+    all sides, density 1.1 rho_f, tau = 1, eps_w = 1, delta = 1, released on
+    the centre line at 0.8 H with its major axis at theta0 from the
+    horizontal.  Gravity 980 cm/s^2 at dx = 0.002 cm and nu = 0.01 cm^2/s
+    (dt = nu_lu dx^2 / nu = 6.67e-5 s) is 2.178e-3 lattice units."""
+    H = 10 * L
+    a = L / 8.0
+    return Workload("ellipse_settling", 2, (L, H, 1), (0, 0, 1), tau=1.0, alpha=1.0,
+                    g_grav=(0.0, -g, 0.0), delta=1.0, eps_p=1.0, eps_w=1.0,
+                    pos=[[0.5 * (L - 1), -0.5 + 0.8 * H]], radius=[a], ratio=[1.1],
+                    minor=[0.5 * a], theta=[theta0], steps=steps)
 
 
 def random_small(seed: int, D: int = 2, n=(24, 20, 1), periodic=(1, 0, 1), nparticles: int = 3,
