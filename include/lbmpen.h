@@ -131,6 +131,28 @@ int lbm_num_instances(const lbm_ctx* ctx);
 int lbm_add_particles(lbm_ctx* ctx, int instance, int n, const double* pos, const double* radius,
                       const double* density_ratio, const double* vel, const double* omega);
 
+/* Add n ellipses to a D2Q9 instance (Sec. 3.3; the paper's third benchmark
+ * settles one).  An ellipse is a particle of semi-axes a (along its
+ * orientation e = (cos theta, sin theta)) and b (along e_perp); node x is
+ * solid iff b^2 (r.e)^2 + a^2 (r.e_perp)^2 <= a^2 b^2, r = x - X, evaluated in
+ * FP64 with separate roundings.  theta advances each step by the trapezoid
+ * of omega (lbm_get_particles returns it).  Eq. 22 is unchanged (in 2D the
+ * moment of inertia is the scalar rho_s sum |r|^2 for any shape).  The
+ * collision forces of Eqs. 19-20, stated for disks, take the ellipse's
+ * support distance sqrt(a^2 (n.e)^2 + b^2 (n.e_perp)^2) along the line of
+ * the force in place of its radius.
+ *   pos   n*2 centres, a n semi-major axes (>= 2, <= max_radius),
+ *   b     n semi-minor axes (1 <= b <= a; b == a is a disk),
+ *   theta n orientations (radians, angle of the a axis from +x) or NULL (0),
+ *   density_ratio, vel, omega as for lbm_add_particles.
+ * Fails with LBM_ERR_INVALID on a D3Q19 context, for axes out of range or a
+ * non-finite orientation, and as lbm_add_particles otherwise.  The discrete
+ * adjoint (lbm_adjoint_forward) does not cover ellipses and returns
+ * LBM_ERR_INVALID on a context that holds one. */
+int lbm_add_ellipses(lbm_ctx* ctx, int instance, int n, const double* pos, const double* a,
+                     const double* b, const double* theta, const double* density_ratio,
+                     const double* vel, const double* omega);
+
 /* Advance every instance by nsteps time steps.  Asynchronous on the context
  * stream; device errors surface at the next lbm_sync.  After the first call
  * the steps are replayed from captured CUDA graphs unless graphs are off. */

@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(256, Q == 9 ? 3 : 2) k_adj_fluid(const InstDes
             cd.R2hi = pr.R2hi;
             cd.p = p;
             cd.k = (int)(e & (MAXK - 1));
+            cd.boff = 0;
+            cd.bh = 0;
+            cd.shape = pr.shape;
             cand[c] = cd;
         }
     }

@@ -72,7 +72,8 @@ struct Instance {
     int maxk = 0;
     DevBuf f[2], prec, lcnt[2], lent[2], lrec[2], ubox, ubox_scratch, boxinfo, btot, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
         Ubar, Xf, Acor;
-    std::vector<double> hR;      // radii (validation)
+    std::vector<double> hR;      // radii, semi-major axes of ellipses (validation)
+    std::vector<double> hB;      // semi-minor axes (== hR for disks and spheres)
     std::vector<double> hratio;  // density ratios (per-particle constants)
     std::vector<int> hbox;       // per particle: first entry of its velocity box, H (pairs)
     long long box_entries = 0;   // entries of all velocity boxes
@@ -342,7 +343,8 @@ int upload_descs(lbm_ctx* ctx) {
 
 // Per-particle constants of the update: 1 - rho_f/rho_s (buoyancy-reduced
 // gravity), C/eps_p and C/eps_w with C = (rho_s - rho_f)|g| (Eqs. 19-20),
-// 1/delta, 1/rho_s (the mass is rho_s times the node count) and R.
+// 1/delta, 1/rho_s (the mass is rho_s times the node count), R and the
+// semi-minor axis B (B == R: disk or sphere).
 int upload_pconst(lbm_ctx* ctx, Instance& I) {
     if (I.np == 0) return LBM_OK;
     const lbm_config& c = I.cfg;
@@ -357,6 +359,7 @@ int upload_pconst(lbm_ctx* ctx, Instance& I) {
         q[PC_INVDELTA] = 1.0 / c.delta;
         q[PC_INVRHOS] = 1.0 / (I.hratio[p] * c.rho_f);
         q[PC_R] = I.hR[p];
+        q[PC_B] = I.hB[p];
     }
     CK(cudaMemcpy(I.pconst.ptr, pc.data(), sizeof(double) * pc.size(), cudaMemcpyHostToDevice));
     return LBM_OK;
@@ -733,8 +736,35 @@ int lbm_num_particles(const lbm_ctx* ctx, int i) {
     return ctx->inst[i].np;
 }
 
-int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const double* radius,
-                      const double* ratio, const double* vel, const double* omega) {
+// Velocity boxes of all particles of an instance (side 2H + 1, H = ceil(R) + 2,
+// one after another), allocated to fit and marked empty (NaN).
+static int layout_boxes(lbm_ctx* ctx, Instance& I) {
+    const int D = ctx->D;
+    I.hbox.clear();
+    I.box_entries = 0;
+    for (int k = 0; k < I.np; ++k) {
+        const int H = (int)ceil(I.hR[k]) + 2, side = 2 * H + 1;
+        I.hbox.push_back((int)I.box_entries);
+        I.hbox.push_back(H);
+        I.box_entries += D == 2 ? (long long)side * side : (long long)side * side * side;
+    }
+    if (I.box_entries >= (1LL << 31)) return set_err(ctx, LBM_ERR_INVALID, "velocity boxes exceed 2^31 entries%s");
+    if (I.np == 0) return LBM_OK;
+    const size_t eb = (size_t)I.box_entries * (D == 2 ? 8 : 16);
+    int rc;
+    if ((rc = dalloc(ctx, I.ubox, eb)) || (rc = dalloc(ctx, I.ubox_scratch, eb))) return rc;
+    CK(cudaMemsetAsync(I.ubox.ptr, 0xff, I.ubox.bytes, ctx->st));  // every entry empty (NaN)
+    CK(cudaMemcpyAsync(I.boxinfo.ptr, I.hbox.data(), sizeof(int) * I.hbox.size(), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return LBM_OK;
+}
+
+// Disks and spheres (minor == NULL) or ellipses (2D; minor = semi-minor axes,
+// theta = orientations or NULL).
+static int add_particles_impl(lbm_ctx* ctx, int i, int n, const double* pos, const double* radius,
+                              const double* minor, const double* theta, const double* ratio,
+                              const double* vel, const double* omega) {
     int rc = check_inst(ctx, i);
     if (rc) return rc;
     ctx->adj.ready = false;
@@ -743,10 +773,15 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
     if (n == 0) return LBM_OK;
     Instance& I = ctx->inst[i];
     const int D = ctx->D;
+    if (minor && D != 2) return set_err(ctx, LBM_ERR_INVALID, "ellipses need the D2Q9 lattice%s");
     if (I.np + n > I.cap) return set_err(ctx, LBM_ERR_INVALID, "max_particles exceeded%s");
     for (int k = 0; k < n; ++k) {
         if (!(radius[k] >= 2.0) || radius[k] > I.cfg.max_radius)
             return set_err(ctx, LBM_ERR_INVALID, "radius must lie in [2, max_radius]%s");
+        if (minor && !(minor[k] >= 1.0 && minor[k] <= radius[k]))
+            return set_err(ctx, LBM_ERR_INVALID, "semi-minor axis must lie in [1, a]%s");
+        if (theta && !(theta[k] == theta[k] && fabs(theta[k]) < 1e6))
+            return set_err(ctx, LBM_ERR_INVALID, "orientation must be finite%s");
         if (!(ratio[k] > 0.0)) return set_err(ctx, LBM_ERR_INVALID, "density ratio must be positive%s");
         for (int d = 0; d < D; ++d) {
             const double x = pos[k * D + d];
@@ -760,7 +795,9 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
         }
     }
     // host staging, FP64 [n][3]
-    std::vector<double> X(3 * n, 0.0), U(3 * n, 0.0), W(3 * n, 0.0), Z(3 * n, 0.0);
+    std::vector<double> X(3 * n, 0.0), U(3 * n, 0.0), W(3 * n, 0.0), Z(3 * n, 0.0), T(3 * n, 0.0);
+    if (theta)
+        for (int k = 0; k < n; ++k) T[3 * k + 2] = theta[k];
     for (int k = 0; k < n; ++k)
         for (int d = 0; d < D; ++d) {
             X[3 * k + d] = pos[k * D + d];
@@ -783,34 +820,33 @@ int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const doubl
     CK(up(I.W, W));
     CK(up(I.Un, U));
     CK(up(I.Wn, W));
-    CK(up(I.theta, Z));
+    CK(up(I.theta, T));
     CK(up(I.A, Z));
     CK(cudaMemcpyAsync(P<double>(I.R) + I.np, radius, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(P<double>(I.ratio) + I.np, ratio, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(P<int>(I.count) + I.np, 0, sizeof(int) * n, ctx->st));
-    // velocity boxes of the new particles: side 2H + 1, H = ceil(R) + 2, after the existing ones
-    for (int k = 0; k < n; ++k) {
-        const int H = (int)ceil(radius[k]) + 2, side = 2 * H + 1;
-        I.hbox.push_back((int)I.box_entries);
-        I.hbox.push_back(H);
-        I.box_entries += D == 2 ? (long long)side * side : (long long)side * side * side;
-    }
-    if (I.box_entries >= (1LL << 31)) return set_err(ctx, LBM_ERR_INVALID, "velocity boxes exceed 2^31 entries%s");
-    {
-        const size_t eb = (size_t)I.box_entries * (D == 2 ? 8 : 16);
-        if ((rc = dalloc(ctx, I.ubox, eb)) || (rc = dalloc(ctx, I.ubox_scratch, eb))) return rc;
-        CK(cudaMemsetAsync(I.ubox.ptr, 0xff, I.ubox.bytes, ctx->st));  // every entry empty (NaN)
-        CK(cudaMemcpyAsync(I.boxinfo.ptr, I.hbox.data(), sizeof(int) * I.hbox.size(), cudaMemcpyHostToDevice,
-                           ctx->st));
-    }
     CK(cudaStreamSynchronize(ctx->st));
     I.np += n;
     I.hR.insert(I.hR.end(), radius, radius + n);
+    if (minor) I.hB.insert(I.hB.end(), minor, minor + n);
+    else I.hB.insert(I.hB.end(), radius, radius + n);
     I.hratio.insert(I.hratio.end(), ratio, ratio + n);
+    if ((rc = layout_boxes(ctx, I))) return rc;
     if ((rc = upload_pconst(ctx, I))) return rc;
     if ((rc = upload_descs(ctx))) return rc;
     invalidate_graphs(ctx);
     return republish(ctx);
+}
+
+int lbm_add_particles(lbm_ctx* ctx, int i, int n, const double* pos, const double* radius,
+                      const double* ratio, const double* vel, const double* omega) {
+    return add_particles_impl(ctx, i, n, pos, radius, nullptr, nullptr, ratio, vel, omega);
+}
+
+int lbm_add_ellipses(lbm_ctx* ctx, int i, int n, const double* pos, const double* a, const double* b,
+                     const double* theta, const double* ratio, const double* vel, const double* omega) {
+    if (n > 0 && !b) return set_err(ctx, LBM_ERR_INVALID, "bad particle arrays%s");
+    return add_particles_impl(ctx, i, n, pos, a, b, theta, ratio, vel, omega);
 }
 
 static int step_impl(lbm_ctx* ctx, int nsteps) {
@@ -980,7 +1016,7 @@ int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes) {
     size_t total = 4 * sizeof(long long);
     for (auto& I : ctx->inst)
         total += sizeof(long long) + ssz * (ctx->Q - 1) * I.qstride +
-                 (size_t)I.np * (sizeof(double) * (7 * 3 + 2) + sizeof(int));
+                 (size_t)I.np * (sizeof(double) * (7 * 3 + 3) + sizeof(int));
     if (!buf) {
         *bytes = total;
         return LBM_OK;
@@ -988,7 +1024,7 @@ int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes) {
     if (*bytes < total) return set_err(ctx, LBM_ERR_INVALID, "state buffer too small%s");
     CK(cudaStreamSynchronize(ctx->st));
     char* w = static_cast<char*>(buf);
-    long long hdr[4] = {0x4c424d50454e31LL, (long long)ctx->inst.size(), ctx->steps, ctx->Q};
+    long long hdr[4] = {0x4c424d50454e32LL, (long long)ctx->inst.size(), ctx->steps, ctx->Q};
     memcpy(w, hdr, sizeof hdr);
     w += sizeof hdr;
     for (auto& I : ctx->inst) {
@@ -1004,6 +1040,8 @@ int lbm_save_state(lbm_ctx* ctx, void* buf, size_t* bytes) {
             w += sizeof(double) * 3 * I.np;
         }
         CK(cudaMemcpy(w, I.R.ptr, sizeof(double) * I.np, cudaMemcpyDeviceToHost));
+        w += sizeof(double) * I.np;
+        memcpy(w, I.hB.data(), sizeof(double) * I.np);
         w += sizeof(double) * I.np;
         CK(cudaMemcpy(w, I.ratio.ptr, sizeof(double) * I.np, cudaMemcpyDeviceToHost));
         w += sizeof(double) * I.np;
@@ -1023,7 +1061,7 @@ int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
     long long hdr[4];
     memcpy(hdr, r, sizeof hdr);
     r += sizeof hdr;
-    if (hdr[0] != 0x4c424d50454e31LL || hdr[1] != (long long)ctx->inst.size() || hdr[3] != ctx->Q)
+    if (hdr[0] != 0x4c424d50454e32LL || hdr[1] != (long long)ctx->inst.size() || hdr[3] != ctx->Q)
         return set_err(ctx, LBM_ERR_INVALID, "state blob does not match this context%s");
     const size_t ssz = ctx->fp16 ? 2 : 4;
     size_t need = sizeof hdr;
@@ -1035,7 +1073,7 @@ int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
             memcpy(&np, q, sizeof np);
             if (np < 0 || np > I.cap) return set_err(ctx, LBM_ERR_INVALID, "particle count exceeds capacity%s");
             const size_t add = sizeof(long long) + ssz * (ctx->Q - 1) * I.qstride +
-                               (size_t)np * (sizeof(double) * 23 + sizeof(int));
+                               (size_t)np * (sizeof(double) * 24 + sizeof(int));
             need += add;
             q += add;
         }
@@ -1058,9 +1096,12 @@ int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes) {
         I.hR.assign(reinterpret_cast<const double*>(r), reinterpret_cast<const double*>(r) + I.np);
         CK(cudaMemcpy(I.R.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
         r += sizeof(double) * I.np;
+        I.hB.assign(reinterpret_cast<const double*>(r), reinterpret_cast<const double*>(r) + I.np);
+        r += sizeof(double) * I.np;
         CK(cudaMemcpy(I.ratio.ptr, r, sizeof(double) * I.np, cudaMemcpyHostToDevice));
         I.hratio.assign(reinterpret_cast<const double*>(r), reinterpret_cast<const double*>(r) + I.np);
         r += sizeof(double) * I.np;
+        if ((rc = layout_boxes(ctx, I))) return rc;
         if ((rc = upload_pconst(ctx, I))) return rc;
         CK(cudaMemcpy(I.count.ptr, r, sizeof(int) * I.np, cudaMemcpyHostToDevice));
         r += sizeof(int) * I.np;
@@ -1218,6 +1259,9 @@ int lbm_adjoint_forward(lbm_ctx* ctx, int nsteps, int seg_len) {
     if (rc) return rc;
     if (nsteps < 1) return set_err(ctx, LBM_ERR_INVALID, "nsteps must be positive%s");
     if (seg_len < 0) return set_err(ctx, LBM_ERR_INVALID, "negative segment length%s");
+    for (const Instance& I : ctx->inst)
+        for (int p = 0; p < I.np; ++p)
+            if (I.hB[p] != I.hR[p]) return set_err(ctx, LBM_ERR_INVALID, "the adjoint covers disks and spheres only%s");
     AdjCtx& A = ctx->adj;
     A.ready = false;
     // an even segment length keeps the parity of the global step equal to that

@@ -120,7 +120,7 @@ struct __align__(16) Cand {
     int k;     // index of this tile among the tiles of the particle's bounding box
     int boff;  // first entry of the particle's velocity box
     int bh;    // H of the box: side 2H + 1, centred on ref
-    int pad;
+    int shape; // 0 disk or sphere, 1 ellipse (the filter reads its record)
 };
 static_assert(sizeof(Cand) == CAND_BYTES, "candidate records are copied in 64-byte units");
 
@@ -159,11 +159,14 @@ __device__ __forceinline__ int wrap_int(int d, int n, int per) {
 // Exact FP64 form of Eq. 9 on the lattice, identical operation by operation
 // to the reference definition: d2 = ((0 + dx*dx) + dy*dy) + dz*dz with each
 // dx = x - X_d taken to the minimum image on periodic axes, then d2 <= R*R.
-// Separate roundings (no fused multiply-add) via the _rn intrinsics.
+// An ellipse (Sec. 3.3, 2D): u = dx cos + dy sin, v = dy cos - dx sin, then
+// b^2 (u u) + a^2 (v v) <= a^2 b^2.  Separate roundings (no fused
+// multiply-add) via the _rn intrinsics.
 template <int D>
 __device__ __noinline__ bool inside_exact(const PRec* __restrict__ pr, int x, int y, int z, int nx,
                                           int ny, int nz, int pmask) {
     const int xyz[3] = {x, y, z}, n[3] = {nx, ny, nz};
+    double r[3] = {0.0, 0.0, 0.0};
     double d2 = 0.0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -173,7 +176,14 @@ __device__ __noinline__ bool inside_exact(const PRec* __restrict__ pr, int x, in
             if (dx > half) dx = __dsub_rn(dx, (double)n[d]);
             else if (dx < -half) dx = __dadd_rn(dx, (double)n[d]);
         }
+        r[d] = dx;
         d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
+    }
+    if (D == 2 && pr->shape) {
+        const double u = __dadd_rn(__dmul_rn(r[0], pr->ec), __dmul_rn(r[1], pr->es));
+        const double v = __dsub_rn(__dmul_rn(r[1], pr->ec), __dmul_rn(r[0], pr->es));
+        const double lhs = __dadd_rn(__dmul_rn(pr->b2, __dmul_rn(u, u)), __dmul_rn(pr->R2, __dmul_rn(v, v)));
+        return lhs <= __dmul_rn(pr->R2, pr->b2);
     }
     return d2 <= pr->R2;
 }
@@ -183,9 +193,37 @@ __device__ __forceinline__ bool inside_exact(const Geo& g, const PRec& pr, const
                            g.per[0] | (g.per[1] << 1) | (g.per[2] << 2));
 }
 
+// Float filter of the indicator of candidate cd at a node: the squared
+// distance against the band [R2lo, R2hi] of the disk (sphere), or for an
+// ellipse inside its circumscribed circle the normalised form
+// (r.e / a)^2 + (r.e_perp / b)^2 against the band [qlo, qhi] (its constants
+// from the particle's record).  Nodes in a band take the exact FP64 test.
+template <int D>
+__device__ __forceinline__ bool inside_filtered(const Geo& in, const Cand& cd, const int* xyz) {
+    float r[3] = {0.f, 0.f, 0.f};
+    float d2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        int di = wrap_int(xyz[d] - cd.ref[d], in.n[d], in.per[d]);
+        r[d] = (float)di - cd.frac[d];
+        d2 = fmaf(r[d], r[d], d2);
+    }
+    if (d2 > cd.R2hi) return false;
+    if (D == 2 && cd.shape) {
+        const PRec& pr = in.prec[cd.p];
+        const float u = fmaf(r[0], pr.fc, r[1] * pr.fs);
+        const float v = fmaf(r[1], pr.fc, -(r[0] * pr.fs));
+        const float q = fmaf(u * u, pr.ia2, (v * v) * pr.ib2);
+        if (q < pr.qlo) return true;
+        if (q > pr.qhi) return false;
+        return inside_exact<D>(in, pr, xyz);
+    }
+    if (d2 < cd.R2lo) return true;
+    return inside_exact<D>(in, in.prec[cd.p], xyz);
+}
+
 // Owner of a node among the tile's candidates: lowest particle index whose
-// solid domain holds the node, or -1.  Float filter with a safety band; nodes
-// in the band take the exact FP64 test.
+// solid domain holds the node, or -1 (float filter, exact test in its band).
 template <int D>
 __device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int ncand,
                                         const int* xyz, int* slot) {
@@ -193,17 +231,7 @@ __device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int nca
     for (int c = 0; c < ncand; ++c) {
         const Cand& cd = cand[c];
         if (best >= 0 && cd.p > best) continue;
-        float d2 = 0.f;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            int di = wrap_int(xyz[d] - cd.ref[d], in.n[d], in.per[d]);
-            float dx = (float)di - cd.frac[d];
-            d2 = fmaf(dx, dx, d2);
-        }
-        bool inside;
-        if (d2 < cd.R2lo) inside = true;
-        else if (d2 > cd.R2hi) inside = false;
-        else inside = inside_exact<D>(in, in.prec[cd.p], xyz);
+        const bool inside = inside_filtered<D>(in, cd, xyz);
         if (inside && (best < 0 || cd.p < best)) {
             best = cd.p;
             bslot = c;
@@ -250,17 +278,7 @@ __device__ __forceinline__ int owner_masked(const Geo& in, const Cand* cand, uns
         act &= act - 1;
         const Cand& cd = cand[c];
         if (best >= 0 && cd.p > best) continue;
-        float d2 = 0.f;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            int di = wrap_int(xyz[d] - cd.ref[d], in.n[d], in.per[d]);
-            float dx = (float)di - cd.frac[d];
-            d2 = fmaf(dx, dx, d2);
-        }
-        bool inside;
-        if (d2 < cd.R2lo) inside = true;
-        else if (d2 > cd.R2hi) inside = false;
-        else inside = inside_exact<D>(in, in.prec[cd.p], xyz);
+        const bool inside = inside_filtered<D>(in, cd, xyz);
         if (inside && (best < 0 || cd.p < best)) {
             best = cd.p;
             bslot = c;

@@ -197,7 +197,7 @@ __device__ __forceinline__ void fluid_tile(const InstDesc& in, int local, int pa
             const int2 bi = in.boxinfo[p];
             cd.boff = bi.x;
             cd.bh = bi.y;
-            cd.pad = 0;
+            cd.shape = pr.shape;
             cand[c] = cd;
         }
         if (commit && tid == 0) in.list_cnt[par ^ 1][local] = 0;

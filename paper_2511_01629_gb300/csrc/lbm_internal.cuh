@@ -110,7 +110,10 @@ constexpr int MAXK = 1 << KBITS;
 enum { ST_DIVERGED = 1, ST_CAPACITY = 2, ST_PARTICLE = 4, ST_DISPLACEMENT = 8, ST_TIMEOUT = 16 };
 
 // Per-particle constants (host-computed, FP64), stride PCONST_N.
-enum { PC_GFAC = 0, PC_CPAIR = 1, PC_CWALL = 2, PC_INVDELTA = 3, PC_INVRHOS = 4, PC_R = 5, PCONST_N = 8 };
+// PC_R is the radius, or the semi-major axis a of an ellipse; PC_B the
+// semi-minor axis b (== R for a disk).
+enum { PC_GFAC = 0, PC_CPAIR = 1, PC_CWALL = 2, PC_INVDELTA = 3, PC_INVRHOS = 4, PC_R = 5, PC_B = 6,
+       PCONST_N = 8 };
 
 // Grid-wide barrier of the particle kernel (all its blocks are resident).
 struct GridBar {
@@ -119,17 +122,28 @@ struct GridBar {
 };
 
 // Particle record read by the fluid kernel; written by the particle kernel
-// for the next step.
+// for the next step.  A disk (sphere) is inside |x - X|^2 <= R^2; an ellipse
+// (2D, shape = 1) with semi-axes a = R and b along e = (cos theta, sin theta)
+// and e_perp is inside b^2 (r.e)^2 + a^2 (r.e_perp)^2 <= a^2 b^2.
 struct __align__(16) PRec {
     double X[3];     // centre X^n (FP64, exact indicator test)
-    double R2;       // R * R
+    double R2;       // R * R (a * a of an ellipse)
     int ref[3];      // floor(X) per axis
     int ntiles;      // tiles of the bounding box (slots written this step)
     float frac[3];   // X - floor(X) as float (filter test)
     float R2lo, R2hi;  // float thresholds: d2 < R2lo inside, d2 > R2hi outside
+                       //   (an ellipse: only d2 > R2hi, its circumscribed circle)
     float a[3];      // solid-node acceleration (1 - rho_f/rho_s) g + A_i
+    int shape;       // 0 disk or sphere, 1 ellipse
     int pad;
+    double ec, es;   // cos, sin of theta^n (ellipse; 1, 0 otherwise)
+    double b2;       // b * b
+    float fc, fs;    // ec, es as float (filter test)
+    float ia2, ib2;  // 1 / a^2, 1 / b^2 as float (filter test)
+    float qlo, qhi;  // float thresholds of (r.e)^2 / a^2 + (r.e_perp)^2 / b^2
+    float pad2[2];
 };
+static_assert(sizeof(PRec) == 144, "particle record layout");
 
 struct InstDesc {
     int n[3];

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_accumulate(NaGrid g, const floa
         PRec pr;
         for (int d = 0; d < 3; ++d) pr.X[d] = Xp[d];
         pr.R2 = Rp * Rp;
+        pr.shape = 0;  // disks and spheres only
         if (ok && ((D == 2) ? inside_exact<2>(&pr, xyz[0], xyz[1], 0, g.n[0], g.n[1], 1, pm)
                             : inside_exact<3>(&pr, xyz[0], xyz[1], xyz[2], g.n[0], g.n[1], g.n[2], pm))) {
             bool mine = true;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_accumulate(NaGrid g, const floa
                 const int j = lower[i];
                 for (int d = 0; d < 3; ++d) q.X[d] = d < D ? X[j * D + d] : 0.0;
                 q.R2 = R[j] * R[j];
+                q.shape = 0;
                 if ((D == 2) ? inside_exact<2>(&q, xyz[0], xyz[1], 0, g.n[0], g.n[1], 1, pm)
                              : inside_exact<3>(&q, xyz[0], xyz[1], xyz[2], g.n[0], g.n[1], g.n[2], pm))
                     mine = false;

@@ -17,6 +17,19 @@ namespace lbmpen {
 constexpr int PB = 8;         // particles per block (one per warp)
 constexpr int XCHUNK = 1024;  // particle positions staged in shared memory at a time
 
+// Extent of a particle along the unit vector (nx, ny): R for a disk; for an
+// ellipse (semi-axes R = a and B = b, orientation (ec, es)) the support
+// distance sqrt(a^2 (n.e)^2 + b^2 (n.e_perp)^2).  Used in place of the radius
+// in Eqs. 19-20, which the paper states for disks.
+__device__ __forceinline__ double extent_along(double R, double B, double ec, double es, double nx,
+                                               double ny) {
+    if (B == R) return R;
+    const double ne = __dadd_rn(__dmul_rn(nx, ec), __dmul_rn(ny, es));
+    const double np = __dsub_rn(__dmul_rn(ny, ec), __dmul_rn(nx, es));
+    return sqrt(__dadd_rn(__dmul_rn(__dmul_rn(R, R), __dmul_rn(ne, ne)),
+                          __dmul_rn(__dmul_rn(B, B), __dmul_rn(np, np))));
+}
+
 // Pair part of Eq. 21 on particle i at two position sets: Xk[src] (F1) and
 // Xk[src] + h Ubar (F2).  The block's particles all belong to one instance;
 // its positions are staged in shared memory in chunks and the lanes split
@@ -47,7 +60,8 @@ __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lan
             near[pass] = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] <= lim * lim;
         }
         if (!near[0] && !near[1]) continue;
-        const double range = in.R[i] + in.R[j] + in.delta;
+        const double Bi = in.pconst[PCONST_N * i + PC_B], Bj = in.pconst[PCONST_N * j + PC_B];
+        const bool ell = Bi != in.R[i] || Bj != in.R[j];
         for (int pass = 0; pass < 2; ++pass) {
             if (!near[pass]) continue;
             const double sh = pass ? h : 0.0;
@@ -64,6 +78,13 @@ __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lan
             }
             const double dij = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])),
                                               __dmul_rn(dd[2], dd[2])));
+            double range = in.R[i] + in.R[j] + in.delta;
+            if (ell && dij > 0.0) {  // ellipses (2D): extents along the line of centres
+                const double nx = dd[0] / dij, ny = dd[1] / dij;
+                const PRec &ri = in.prec[i], &rj = in.prec[j];
+                range = extent_along(in.R[i], Bi, ri.ec, ri.es, nx, ny) +
+                        extent_along(in.R[j], Bj, rj.ec, rj.es, nx, ny) + in.delta;
+            }
             if (dij <= range) {
                 const double sc = (range - dij) * inv_delta;
                 double* f = pass ? f2 : f1;
@@ -92,7 +113,8 @@ __device__ void gather_pairs(const double* f1, const double* f2, double* F1, dou
 }
 
 // Wall part of Eq. 21 (mirror images across the planes -1/2 and n - 1/2),
-// component d of the force on a particle at coordinate Xi along axis d.
+// component d of the force on a particle at coordinate Xi along axis d; Ri is
+// the particle's extent along axis d (its radius, for a disk).
 __device__ void wall_force_d(const InstDesc& in, int d, double Xi, double& F, double cw, double inv_delta,
                              double Ri) {
     if (cw == 0.0) return;  // cw = C / eps_w of the particle
@@ -187,23 +209,46 @@ __device__ __forceinline__ RecComp record_component(const InstDesc& in, int d, i
     return r;
 }
 
-// The radius fields and tile count of a record (nt tiles of the bounding box).
-__device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, double R, int nt) {
+// The size and shape fields and tile count of a record (nt tiles of the
+// bounding box).  R is the radius or the semi-major axis a, B the semi-minor
+// axis b (B == R: a disk or sphere).  The ellipse filter band: its float form
+// (r.e / a)^2 + (r.e_perp / b)^2 carries a relative error below
+// ~1e-6 (1 + a/b) within the circumscribed circle, and the band is ten times
+// that.
+__device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, double R, double B, int nt) {
     const float Rf = (float)R;
     pr.R2 = R * R;
     const float R2f = Rf * Rf;
     pr.R2lo = R2f * (1.0f - 2e-5f) - 2e-4f;
     pr.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
     pr.ntiles = nt;
+    pr.shape = B != R;
     pr.pad = 0;
+    pr.b2 = B * B;
+    pr.ia2 = (float)(1.0 / (R * R));
+    pr.ib2 = (float)(1.0 / (B * B));
+    const float beta = 1e-5f * (1.0f + (float)(R / B));
+    pr.qlo = 1.0f - beta;
+    pr.qhi = 1.0f + beta;
+    pr.pad2[0] = pr.pad2[1] = 0.f;
     if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
 }
 
-// Record of particle p from its state (X, A) and constants (R, 1 - rho_f/rho_s),
-// with the tiles of its bounding box (slots k enumerate them x-fastest; no tile
-// is listed twice).  One thread.
+// Orientation fields of a record: cos and sin of theta (the z component of
+// the orientation in 2D) for an ellipse; (1, 0) otherwise.
+__device__ __forceinline__ void record_orientation(PRec& pr, bool ellipse, double theta) {
+    pr.ec = ellipse ? cos(theta) : 1.0;
+    pr.es = ellipse ? sin(theta) : 0.0;
+    pr.fc = (float)pr.ec;
+    pr.fs = (float)pr.es;
+}
+
+// Record of particle p from its state (X, A, theta) and constants (R, B,
+// 1 - rho_f/rho_s), with the tiles of its bounding box (slots k enumerate them
+// x-fastest; no tile is listed twice).  One thread.
 __device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& sh, AxisTiles* at,
-                                 const double* Xp, const double* Ap, double R, float gfac) {
+                                 const double* Xp, const double* Ap, double R, double B, double theta,
+                                 float gfac) {
     PRec pr;
     int nt = 1;
     for (int d = 0; d < 3; ++d) {
@@ -215,7 +260,8 @@ __device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& 
         at[d] = r.t;
         nt *= r.t.na + r.t.nb;
     }
-    record_radius(in, pr, R, nt);
+    record_radius(in, pr, R, B, nt);
+    record_orientation(pr, B != R, theta);
     in.prec_out[p] = pr;
 }
 
@@ -226,6 +272,7 @@ __device__ void make_record(const InstDesc& in, int p, int D, const Shape& sh, A
         A[d] = in.A[3 * p + d];
     }
     make_record_from(in, p, D, sh, at, X, A, in.pconst[PCONST_N * p + PC_R],
+                     in.pconst[PCONST_N * p + PC_B], in.theta[3 * p + 2],
                      (float)in.pconst[PCONST_N * p + PC_GFAC]);
 }
 
@@ -252,7 +299,7 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
     const int2 bi = in.boxinfo[p];
     cd.boff = bi.x;
     cd.bh = bi.y;
-    cd.pad = 0;
+    cd.shape = pr.shape;
     Cand* rec = static_cast<Cand*>(in.list_rec[lpar]);
     for (int k = lane; k < nt && k < in.maxk; k += nl) {
         const int kx = k % cnt[0], ky = (k / cnt[0]) % cnt[1], kz = k / (cnt[0] * cnt[1]);
@@ -289,13 +336,21 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
     double F1 = F1in[d], F2 = F2in[d];
     const double* pc = in.pconst + PCONST_N * i;
     const double invrhos = pc[PC_INVRHOS], cw = pc[PC_CWALL], idl = pc[PC_INVDELTA], Ri = pc[PC_R];
+    const double Bi = pc[PC_B];
     const double gfac = pc[PC_GFAC];
     const double invc = in.invc[i];
     const int cnt = in.count[i];
     const double invM = invrhos * invc;  // 1 / (rho_s n)
     const double Xst = fma(h, Ub, X0);
-    wall_force_d(in, d, X0, F1, cw, idl, Ri);
-    wall_force_d(in, d, Xst, F2, cw, idl, Ri);
+    // extent along axis d: the radius, or for an ellipse at theta^n (this
+    // step's record) its support distance normal to the walls of axis d
+    double Rd = Ri;
+    if (Bi != Ri && d < 2) {
+        const PRec& rn = in.prec[i];
+        Rd = d == 0 ? extent_along(Ri, Bi, rn.ec, rn.es, 1.0, 0.0) : extent_along(Ri, Bi, rn.ec, rn.es, 0.0, 1.0);
+    }
+    wall_force_d(in, d, X0, F1, cw, idl, Rd);
+    wall_force_d(in, d, Xst, F2, cw, idl, Rd);
     const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
     const double cor = c * (F1 + F2);      // this sub-step's correction
     const double Xn = Xst + cor;
@@ -358,7 +413,8 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
         pr.frac[d] = r.frac;
         pr.a[d] = r.a;
         at[d] = r.t;
-        if (d == 0) record_radius(in, pr, Ri, nt);
+        if (d == 0) record_radius(in, pr, Ri, Bi, nt);
+        if (d == 2) record_orientation(pr, Bi != Ri, Tn);
     }
 }
 

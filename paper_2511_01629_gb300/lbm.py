@@ -101,6 +101,7 @@ def lib():
                                        C.POINTER(_vp)]),
         "lbm_num_instances": (C.c_int, [_vp]),
         "lbm_add_particles": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+        "lbm_add_ellipses": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lbm_step": (C.c_int, [_vp, C.c_int]),
         "lbm_sync": (C.c_int, [_vp]),
         "lbm_get_fields": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int]),
@@ -269,6 +270,16 @@ class LBM:
         self._check(lib().lbm_add_particles(self._h, i, len(radius), _ptr(pos), _ptr(radius),
                                             _ptr(ratio), _ptr(vel), _ptr(omega)))
 
+    def add_ellipses(self, i, pos, a, b, theta, ratio, vel=None, omega=None):
+        """Ellipses (D2Q9): semi-axes a >= b, orientation theta (radians)."""
+        f64 = lambda v: np.ascontiguousarray(v, np.float64).reshape(-1)
+        pos, a, b, ratio = f64(pos), f64(a), f64(b), f64(ratio)
+        theta = None if theta is None else f64(theta)
+        vel = None if vel is None else f64(vel)
+        omega = None if omega is None else f64(omega)
+        self._check(lib().lbm_add_ellipses(self._h, i, len(a), _ptr(pos), _ptr(a), _ptr(b), _ptr(theta),
+                                           _ptr(ratio), _ptr(vel), _ptr(omega)))
+
     def step(self, n=1):
         self._check(lib().lbm_step(self._h, int(n)))
 
@@ -418,6 +429,8 @@ def from_workloads(workloads: Sequence, storage=LBM_FP32, add_particles=True, **
     sim = LBM([config_from_workload(w, storage) for w in ws], **kw)
     if add_particles:
         for i, w in enumerate(ws):
-            if w.num_particles:
+            if w.num_particles and getattr(w, "minor", None) is not None:
+                sim.add_ellipses(i, w.pos, w.radius, w.minor, w.theta, w.ratio)
+            elif w.num_particles:
                 sim.add_particles(i, w.pos, w.radius, w.ratio)
     return sim

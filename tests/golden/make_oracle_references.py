@@ -33,7 +33,14 @@ GPU test suite (a 400 x 1600 oracle step takes ~30 ms on 8 cores):
       200 x 800 closed channel, D = 20, ratio 1.01, 12,000 steps: every 100
       steps the step count and, per disk, X, Y, U_x, U_y, omega, count.
 
-  python tests/golden/make_oracle_references.py [trajectory|fd|couette|dkt|all]
+  ellipse_settling_l200.txt
+      A single ellipse settling in a vertical channel (Sec. 3.3;
+      workloads.ellipse_settling): 200 x 2000 closed channel, semi-axes 25
+      and 12.5, ratio 1.1, released on the centre line at 45 degrees, 30,000
+      steps: every 100 steps the step count, X, Y, U_x, U_y, omega, theta and
+      the node count.
+
+  python tests/golden/make_oracle_references.py [trajectory|fd|couette|dkt|ellipse|all]
 """
 import hashlib
 import os
@@ -51,6 +58,7 @@ from paper_2511_01629_gb300 import workloads as W  # noqa: E402
 TRAJ = os.path.join(HERE, "single_disk_seed0_trajectory.txt")
 COUETTE = os.path.join(HERE, "couette_migration_h40.txt")
 DKT = os.path.join(HERE, "dkt_l200.txt")
+ELLIPSE = os.path.join(HERE, "ellipse_settling_l200.txt")
 FD = os.path.join(HERE, "adjoint_disk_seed0_fd.txt")
 EVERY = 50
 
@@ -175,6 +183,26 @@ def dkt():
         fh.write(text)
 
 
+def ellipse():
+    w = W.ellipse_settling()
+    s = oracle.Sim(_config(w), parallel=True)
+    s.add_ellipses(w.pos, w.radius, w.minor, w.theta, w.ratio)
+    rows = []
+    for n in range(0, w.steps + 1, 100):
+        if n:
+            s.step(100)
+        p = s.particles()
+        rows.append((n, *p["X"][0, :2], *p["U"][0, :2], p["W"][0, 2], p["theta"][0, 2], p["count"][0]))
+    s.close()
+    with open(ELLIPSE, "w") as fh:
+        fh.write("# ellipse_settling: 200 x 2000 closed channel, semi-axes a = 25, b = 12.5, ratio 1.1,\n"
+                 "# gravity 2.178e-3, tau = 1, eps_w = 1, delta = 1, released at (99.5, 1599.5) with\n"
+                 "# theta = pi/4; FP64 oracle (tests/golden/make_oracle_references.py).\n"
+                 "# step X Y U_x U_y omega theta count\n")
+        for r in rows:
+            fh.write("%d %.17g %.17g %.17g %.17g %.17g %.17g %d\n" % r)
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "all"
     oracle.build(parallel=True)
@@ -186,3 +214,5 @@ if __name__ == "__main__":
         couette()
     if what in ("dkt", "all"):
         dkt()
+    if what in ("ellipse", "all"):
+        ellipse()

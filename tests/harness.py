@@ -11,6 +11,16 @@ def oracle_config(w):
                               eps_p=w.eps_p, eps_w=w.eps_w, K=w.K)
 
 
+def add_oracle_particles(ref, w):
+    """The workload's disks, spheres or ellipses in an oracle Sim."""
+    if not w.num_particles:
+        return
+    if getattr(w, "minor", None) is not None:
+        ref.add_ellipses(w.pos, w.radius, w.minor, w.theta, w.ratio)
+    else:
+        ref.add_particles(w.pos, w.radius, w.ratio)
+
+
 def make_pair(w, storage=lbm.LBM_FP32, f0=None, graphs=0, shape=None, parallel=False):
     """(gpu context, oracle sim) for workload w, optionally from populations f0 [Q, ...].
     parallel: the oracle's OpenMP build (identical results, all host cores)."""
@@ -23,8 +33,7 @@ def make_pair(w, storage=lbm.LBM_FP32, f0=None, graphs=0, shape=None, parallel=F
         f32 = np.asarray(f0, np.float32)
         sim.set_populations(f32)
         ref.set_f(f32.astype(np.float64))
-    if w.num_particles:
-        ref.add_particles(w.pos, w.radius, w.ratio)
+    add_oracle_particles(ref, w)
     return sim, ref
 
 
@@ -76,8 +85,7 @@ def compare_particles(sim, ref, i=0):
 def oracle_run(w, steps, parallel=True):
     """Fields and particles of the oracle after `steps` steps of workload w."""
     ref = oracle.Sim(oracle_config(w), parallel=parallel)
-    if w.num_particles:
-        ref.add_particles(w.pos, w.radius, w.ratio)
+    add_oracle_particles(ref, w)
     ref.step(steps)
     out = ref.fields(), ref.particles()
     ref.close()

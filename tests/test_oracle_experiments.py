@@ -12,11 +12,15 @@ by what the physics fixes rather than by the oracle itself:
   * two disks released one above the other draft, kiss and tumble
     (Sec. 3.4): the upper disk falls faster in the wake of the lower one,
     the two stay in contact range for a while, and then the upper one passes
-    the lower one and they separate sideways.
+    the lower one and they separate sideways;
+  * an ellipse released at 45 degrees in a vertical channel (Sec. 3.3)
+    turns broadside, swings off the centre line and back, and settles on it
+    at Re ~ 11 (the paper reports 11 for this case).
 
 The stored trajectories (tests/golden/make_oracle_references.py) are
 recomputed here over their first rows, bit for bit.
 """
+import math
 import os
 
 import numpy as np
@@ -156,3 +160,45 @@ def test_dkt_reference_drafts_kisses_and_tumbles():
     after = t > t[swap] + 1000
     assert np.all(np.abs(X0[after] - X1[after]) > 2 * (2 * R))
     assert np.all(Y0[after] < Y1[after])
+
+
+def _ellipse_rows(upto):
+    w = W.ellipse_settling()
+    s = oracle.Sim(_config(w), parallel=True)
+    s.add_ellipses(w.pos, w.radius, w.minor, w.theta, w.ratio)
+    out = []
+    for n in range(0, upto + 1, 100):
+        if n:
+            s.step(100)
+        p = s.particles()
+        out.append([n, *p["X"][0, :2], *p["U"][0, :2], p["W"][0, 2], p["theta"][0, 2], p["count"][0]])
+    s.close()
+    return np.array(out, dtype=np.float64)
+
+
+def test_ellipse_reference_matches_the_oracle():
+    ref = _load("ellipse_settling_l200.txt")
+    got = _ellipse_rows(200)
+    assert np.array_equal(got, ref[: len(got)])
+
+
+def test_ellipse_reference_settles_broadside_on_the_centre_line():
+    """Stored run of workloads.ellipse_settling (a = 25, b = 12.5, L = 8 a,
+    ratio 1.1, 30,000 steps): the major axis starts at 45 degrees and ends
+    horizontal (|sin theta| < 0.05 over the last 30 % of the run); the
+    ellipse first drifts more than 10 lattice units off the centre line and
+    comes back within 2; its settling velocity over the last 20 % gives
+    Re = 2 a U / nu between 10 and 14 (nu = 1/6 at tau = 1)."""
+    r = _load("ellipse_settling_l200.txt")
+    t, x, uy, th = r[:, 0], r[:, 1], r[:, 4], r[:, 6]
+    xc = 99.5
+    assert abs(th[0] - math.pi / 4) < 1e-15
+    late = t > 0.7 * t[-1]
+    assert np.all(np.abs(np.sin(th[late])) < 0.05)
+    assert np.abs(x - xc).max() > 10.0
+    assert abs(x[-1] - xc) < 2.0
+    tail = t > 0.8 * t[-1]
+    Re = 2 * 25.0 * np.abs(uy[tail]).mean() * 6.0
+    assert 10.0 < Re < 14.0, Re
+    # the node count stays that of the ellipse (pi a b = 981.7)
+    assert np.all(np.abs(r[1:, 7] - math.pi * 25 * 12.5) < 15)
