@@ -310,7 +310,11 @@ def main():
             sim.set_kernel_shape(*[int(v) for v in args.shape.split(",")])
         elif args.autotune:
             sim.autotune(3)
-        sim.set_graphs(16)
+        # every timed step replays a captured graph (graphs hold an even number
+        # of steps): G = 16, or the whole run up to 256 steps (all but one when
+        # the run is odd)
+        G = 16 if steps % 16 == 0 or steps > 256 else steps - steps % 2
+        sim.set_graphs(G)
         stream = sim.stream
         nodes = sim.total_nodes
         out = {"nodes": nodes, "shape": sim.kernel_shape(), "launches_per_step": sim.launches_per_step()}
@@ -320,6 +324,12 @@ def main():
             torch.cuda.synchronize()
             return out, sim
         sim.step(warmup)
+        # capture the graph outside the timed region (an even G returns to the
+        # same parity, so one graph serves every replay)
+        if G:
+            sim.step(G)
+        out["graph_steps"] = G
+        out["capture_steps"] = G
         sim.sync()
         torch.cuda.synchronize()
         barrier()
@@ -336,18 +346,27 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         out.update(ms=ms, clocks=clk.summary())
         if with_kernel:
-            # the dominant kernel alone, same stream, averaged over launches
+            # the dominant kernel alone, back to back on the library's stream
+            # (lbm_fluid_step_only), CUDA events around kn launches
+            kn = max(20, min(steps, 2000))
             for _ in range(3):
                 sim.fluid_step_only()
             torch.cuda.synchronize()
             k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            kn = min(steps, 2000)
             k0.record(stream)
             for _ in range(kn):
                 sim.fluid_step_only()
             k1.record(stream)
             torch.cuda.synchronize()
             out["kernel_ms"] = k0.elapsed_time(k1) / kn
+            out["kernel_launches_timed"] = kn
+            # per-kernel breakdown of a step, launched one by one with events
+            # between the kernels (each duration includes its launch latency)
+            sim.step_timed(3)
+            fl, bx, pt = sim.step_timed(kn)
+            out["step_kernels_ms"] = {"fluid": fl, "box_sums": bx, "particles": pt, "steps": kn,
+                                      "note": "steps launched one by one without graphs, CUDA events "
+                                              "between the kernels (lbm_step_timed)"}
         if with_e2e:
             blob = sim.save_state()
             pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
@@ -398,6 +417,8 @@ def main():
         e[3].record(st)
         torch.cuda.synchronize()
         kms = e[2].elapsed_time(e[3]) / 100
+        sim.step_timed(3)
+        kfl, kbox, kpart = sim.step_timed(100)  # per-kernel breakdown of un-graphed steps
         nodes = sim.total_nodes
         bpn = bytes_per_node(ws[0].D, "fp32")
         peak, kind = measured_peak()
@@ -408,7 +429,9 @@ def main():
                 "ms_per_step": ms / steps, "config": describe(name, ws, "fp32"),
                 "kernel_shape": {"vec": shape[0], "tile_rows": shape[1], "warps": shape[2]},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                             "kernel_ms": kms, "algorithmic_bytes_per_node": bpn, "peak_kind": f"hbm_gbs of {kind}"}}
+                             "kernel_ms": kms, "algorithmic_bytes_per_node": bpn,
+                             "peak_kind": f"hbm_gbs of {kind}"},
+                "step_kernels_ms": {"fluid": kfl, "box_sums": kbox, "particles": kpart, "steps": 100}}
 
     storage = args.storage
     res, sim = leg(storage, args.steps, args.warmup, not args.no_e2e, True)
@@ -440,7 +463,12 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_fluid_tma (fused stream-collide-penalize)",
                      "algorithmic_bytes_per_node": bpn, "kernel_ms": kms,
+                     "kernel_timing": "CUDA events around %d back-to-back launches of the fluid kernel "
+                                      "alone (lbm_fluid_step_only) on the library's stream"
+                                      % res["kernel_launches_timed"],
                      "peak_kind": f"hbm_gbs of {peak_kind}"},
+        "step_kernels_ms": res["step_kernels_ms"],
+        "graph_steps": res["graph_steps"], "capture_steps": res["capture_steps"],
         "gpu_launches": res["launches_per_step"] * args.steps,
         "clocks": res["clocks"],
         "kernel_shape": {"vec": res["shape"][0], "tile_rows": res["shape"][1], "warps": res["shape"][2]},
@@ -463,6 +491,7 @@ def main():
                                              traffic_per_launch("fp16", args.workload, r16["shape"])},
                                 "kernel_shape": {"vec": r16["shape"][0], "tile_rows": r16["shape"][1],
                                                  "warps": r16["shape"][2]},
+                                "step_kernels_ms": r16["step_kernels_ms"],
                                 "speedup_vs_fp32": v16 / value}
     if not args.no_other_workloads and args.workload == "many_disks":
         line["other_workloads"] = {name: other_leg(name) for name in ("ensemble", "spheres3d")}

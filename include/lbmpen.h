@@ -205,14 +205,14 @@ int lbm_autotune(lbm_ctx* ctx, int reps);
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);
 int lbm_set_kernel_shape(lbm_ctx* ctx, int vec, int tile_rows, int warps);
 /* Bound on each wait of the particle kernel at its grid-wide barrier between
- * the phases of a step (projection, sub-steps of Algorithm 1); default 2 s.  A
- * wait that runs out records LBM_ERR_TIMEOUT, the kernel returns, lbm_sync
- * reports it and the context then refuses further work (LBM_ERR_STATE).
- * With 0 s a block that does not find the barrier open on its first look
- * gives up at once: with more than one particle block (more than 8
- * particles) a step then times out for certain, which exercises the timeout
- * path without a stalled GPU.  The fluid kernel's waits keep their own 2 s
- * bound.  seconds in [0, 60]. */
+ * the sub-steps of Algorithm 1 (K > 1; with K = 1 the step has no such
+ * barrier); default 2 s.  A wait that runs out records LBM_ERR_TIMEOUT, the
+ * kernel returns, lbm_sync reports it and the context then refuses further
+ * work (LBM_ERR_STATE).  With 0 s a block that does not find the barrier
+ * open on its first look gives up at once: with K > 1 and more than one
+ * particle block (more than 8 particles) a step then times out for certain,
+ * which exercises the timeout path without a stalled GPU.  The fluid
+ * kernel's waits keep their own 2 s bound.  seconds in [0, 60]. */
 int lbm_set_particle_wait_limit(lbm_ctx* ctx, double seconds);
 /* Kernel launches issued by one lbm_step(ctx, 1): the fluid kernel, then with
  * particles the box sums of Eq. 22 and the particle kernel (one launch, or one
@@ -225,6 +225,17 @@ int lbm_launches_per_step(const lbm_ctx* ctx);
  * API exposes (populations, particles, tile lists) is unchanged.  Returns
  * after enqueueing. */
 int lbm_fluid_step_only(lbm_ctx* ctx);
+
+/* Measurement: nsteps time steps exactly like lbm_step (the state advances),
+ * launched one by one without graphs, with CUDA events on the context stream
+ * around each kernel of the step.  Writes the mean duration per step, in ms,
+ * of the fluid kernel, of the box sums (Eq. 22) and of the particle kernel
+ * (Algorithm 1); any pointer may be NULL; 0 for the particle kernels when
+ * there are no particles.  Each duration runs from the end of the previous
+ * kernel to the end of this one, so it includes the launch latency.
+ * Synchronises; nsteps in [1, 100000] (LBM_ERR_INVALID otherwise); returns
+ * the device status like lbm_sync. */
+int lbm_step_timed(lbm_ctx* ctx, int nsteps, float* ms_fluid, float* ms_box, float* ms_particles);
 long long lbm_steps_done(const lbm_ctx* ctx);
 long long lbm_total_nodes(const lbm_ctx* ctx);
 

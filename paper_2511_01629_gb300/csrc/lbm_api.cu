@@ -71,7 +71,7 @@ struct Instance {
     int ntiles = 0, tile0 = 0;
     int maxk = 0;
     DevBuf f[2], prec, lcnt[2], lent[2], lrec[2], ubox, ubox_scratch, boxinfo, btot, X, U, W, Un, Wn, theta, A, R, ratio, count, Xk, pconst, Xsf, invc,
-        Ubar, Xf, Acor;
+        Ubar, Xf, Acor, rconst;
     std::vector<double> hR;      // radii, semi-major axes of ellipses (validation)
     std::vector<double> hB;      // semi-minor axes (== hR for disks and spheres)
     std::vector<double> hratio;  // density ratios (per-particle constants)
@@ -292,6 +292,7 @@ InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {
     d.Acor = P<double>(I.Acor);
     d.Xf = P<float>(I.Xf);
     d.pconst = P<double>(I.pconst);
+    d.rconst = P<RecConst>(I.rconst);
     d.Xsf = P<float>(I.Xsf);
     d.invc = P<double>(I.invc);
     d.rho_f = c.rho_f;
@@ -362,6 +363,29 @@ int upload_pconst(lbm_ctx* ctx, Instance& I) {
         q[PC_B] = I.hB[p];
     }
     CK(cudaMemcpy(I.pconst.ptr, pc.data(), sizeof(double) * pc.size(), cudaMemcpyHostToDevice));
+    // record fields that depend only on the size and shape: R^2 and B^2 as the
+    // exact test of Eq. 9 takes them, and the float bands of its filter.  The
+    // ellipse band: the float form (r.e / a)^2 + (r.e_perp / b)^2 carries a
+    // relative error below ~1e-6 (1 + a/b) within the circumscribed circle,
+    // and the band is ten times that.
+    std::vector<RecConst> rc((size_t)I.np);
+    for (int p = 0; p < I.np; ++p) {
+        const double R = I.hR[p], B = I.hB[p];
+        RecConst& r = rc[p];
+        r.R2 = R * R;
+        r.b2 = B * B;
+        const float Rf = (float)R, R2f = Rf * Rf;
+        r.R2lo = R2f * (1.0f - 2e-5f) - 2e-4f;
+        r.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
+        r.ia2 = (float)(1.0 / (R * R));
+        r.ib2 = (float)(1.0 / (B * B));
+        const float beta = 1e-5f * (1.0f + (float)(R / B));
+        r.qlo = 1.0f - beta;
+        r.qhi = 1.0f + beta;
+        r.shape = B != R;
+        r.pad = 0;
+    }
+    CK(cudaMemcpy(I.rconst.ptr, rc.data(), sizeof(RecConst) * rc.size(), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -585,7 +609,7 @@ void destroy_all(lbm_ctx* ctx) {
         DevBuf* bufs[] = {&I.f[0], &I.f[1], &I.prec, &I.lcnt[0], &I.lcnt[1], &I.lent[0], &I.lent[1],
                           &I.lrec[0], &I.lrec[1],
                           &I.ubox, &I.ubox_scratch, &I.boxinfo, &I.btot, &I.X, &I.U, &I.W, &I.Un, &I.Wn, &I.theta, &I.A, &I.R,
-                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc, &I.Acor};
+                          &I.ratio, &I.count, &I.Xk, &I.Ubar, &I.Xf, &I.pconst, &I.Xsf, &I.invc, &I.Acor, &I.rconst};
         for (DevBuf* b : bufs) dfree(ctx, *b);
     }
     dfree(ctx, ctx->d_insts);
@@ -610,6 +634,7 @@ int alloc_particles(lbm_ctx* ctx, Instance& I, int cap) {
     if ((rc = dalloc(ctx, I.Xk, sizeof(double) * 6 * c))) return rc;
     if ((rc = dalloc(ctx, I.Xf, sizeof(float) * 8 * c))) return rc;
     if ((rc = dalloc(ctx, I.pconst, sizeof(double) * PCONST_N * c))) return rc;
+    if ((rc = dalloc(ctx, I.rconst, sizeof(RecConst) * c))) return rc;
     if ((rc = dalloc(ctx, I.invc, sizeof(double) * c))) return rc;
     if ((rc = dalloc(ctx, I.Xsf, sizeof(float) * 8 * c))) return rc;
     if ((rc = dalloc(ctx, I.boxinfo, sizeof(int2) * c))) return rc;
@@ -900,6 +925,55 @@ int lbm_fluid_step_only(lbm_ctx* ctx) {
     int rc = check_ctx(ctx);
     if (rc) return rc;
     return enqueue_fluid(ctx, 0);
+}
+
+int lbm_step_timed(lbm_ctx* ctx, int nsteps, float* ms_fluid, float* ms_box, float* ms_particles) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (nsteps < 1 || nsteps > 100000) return set_err(ctx, LBM_ERR_INVALID, "nsteps must lie in [1, 100000]%s");
+    const int ne = 4 * nsteps;
+    std::vector<cudaEvent_t> ev(ne, nullptr);
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < ne && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) --made;
+    const bool parts = ctx->np_total > 0;
+    double t[3] = {0, 0, 0};
+    for (int s = 0; s < nsteps && e == cudaSuccess && rc == LBM_OK; ++s) {
+        cudaEvent_t* q = &ev[4 * s];
+        e = cudaEventRecord(q[0], ctx->st);
+        if (e == cudaSuccess) rc = enqueue_fluid(ctx, 1, ctx->st);
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaEventRecord(q[1], ctx->st);
+        if (parts && rc == LBM_OK && e == cudaSuccess)
+            e = launch_box_sums(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D, ctx->st);
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaEventRecord(q[2], ctx->st);
+        if (parts && rc == LBM_OK && e == cudaSuccess) {
+            const bool fused = (ctx->np_total + 7) / 8 <= particle_blocks_resident(ctx->num_sms);
+            e = launch_particles(P<InstDesc>(ctx->d_insts), P<PartRef>(ctx->d_refs), ctx->np_total, ctx->D,
+                                 ctx->inst[0].cfg.K, ctx->par ^ 1, ctx->shape, P<GridBar>(ctx->d_gridbar), fused,
+                                 ctx->st, ctx->wait_ns);
+        }
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaEventRecord(q[3], ctx->st);
+        if (rc == LBM_OK && e == cudaSuccess) {
+            ctx->par ^= 1;
+            ctx->steps += 1;
+        }
+    }
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaStreamSynchronize(ctx->st);
+    for (int s = 0; s < nsteps && e == cudaSuccess && rc == LBM_OK; ++s) {
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[4 * s + k], ev[4 * s + k + 1]);
+            t[k] += ms;
+        }
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    if (rc != LBM_OK) return rc;
+    if (e != cudaSuccess) return cuda_err(ctx, e, "lbm_step_timed");
+    if (ms_fluid) *ms_fluid = (float)(t[0] / nsteps);
+    if (ms_box) *ms_box = (float)(t[1] / nsteps);
+    if (ms_particles) *ms_particles = (float)(t[2] / nsteps);
+    return read_status(ctx);
 }
 
 int lbm_get_fields(lbm_ctx* ctx, int i, float* u, float* p, int* owner, int on_device) {

@@ -145,6 +145,16 @@ struct __align__(16) PRec {
 };
 static_assert(sizeof(PRec) == 144, "particle record layout");
 
+// The fields of a particle's record that depend only on its size and shape,
+// computed on the host when it is added (R2 = R * R and b2 = B * B exactly as
+// the exact test needs them) and copied into every new record.
+struct RecConst {
+    double R2, b2;
+    float R2lo, R2hi, ia2, ib2, qlo, qhi;
+    int shape, pad;
+};
+static_assert(sizeof(RecConst) == 48, "record constants layout");
+
 struct InstDesc {
     int n[3];
     int pitch;
@@ -189,6 +199,7 @@ struct InstDesc {
     double* Acor;             // [np][3] sum of the sub-step corrections of Algorithm 1 (K > 1)
     float* Xf;                // [2][np][4] float copy of X^{k} (w = R) for the pair filter
     float* Xsf;               // [2][np][4] float copy of X^{k} + Ubar/K (w = R): predicted positions
+    const RecConst* rconst;   // [np] size and shape fields of the records
     double* pconst;           // [np][8]: 1 - rho_f/rho_s, C/eps_p, C/eps_w, 1/delta,
                               //   1/(rho_s rho_f... see PCONST_*), R
     double* invc;             // [np] 1 / (solid nodes at step n)

@@ -209,27 +209,20 @@ __device__ __forceinline__ RecComp record_component(const InstDesc& in, int d, i
     return r;
 }
 
-// The size and shape fields and tile count of a record (nt tiles of the
-// bounding box).  R is the radius or the semi-major axis a, B the semi-minor
-// axis b (B == R: a disk or sphere).  The ellipse filter band: its float form
-// (r.e / a)^2 + (r.e_perp / b)^2 carries a relative error below
-// ~1e-6 (1 + a/b) within the circumscribed circle, and the band is ten times
-// that.
-__device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, double R, double B, int nt) {
-    const float Rf = (float)R;
-    pr.R2 = R * R;
-    const float R2f = Rf * Rf;
-    pr.R2lo = R2f * (1.0f - 2e-5f) - 2e-4f;
-    pr.R2hi = R2f * (1.0f + 2e-5f) + 2e-4f;
+// The size and shape fields of particle p's record (host-computed, RecConst)
+// and its tile count (nt tiles of the bounding box).
+__device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, const RecConst& rc, int nt) {
+    pr.R2 = rc.R2;
+    pr.R2lo = rc.R2lo;
+    pr.R2hi = rc.R2hi;
     pr.ntiles = nt;
-    pr.shape = B != R;
+    pr.shape = rc.shape;
     pr.pad = 0;
-    pr.b2 = B * B;
-    pr.ia2 = (float)(1.0 / (R * R));
-    pr.ib2 = (float)(1.0 / (B * B));
-    const float beta = 1e-5f * (1.0f + (float)(R / B));
-    pr.qlo = 1.0f - beta;
-    pr.qhi = 1.0f + beta;
+    pr.b2 = rc.b2;
+    pr.ia2 = rc.ia2;
+    pr.ib2 = rc.ib2;
+    pr.qlo = rc.qlo;
+    pr.qhi = rc.qhi;
     pr.pad2[0] = pr.pad2[1] = 0.f;
     if (nt > in.maxk) atomicOr(in.status, ST_CAPACITY);
 }
@@ -237,10 +230,12 @@ __device__ __forceinline__ void record_radius(const InstDesc& in, PRec& pr, doub
 // Orientation fields of a record: cos and sin of theta (the z component of
 // the orientation in 2D) for an ellipse; (1, 0) otherwise.
 __device__ __forceinline__ void record_orientation(PRec& pr, bool ellipse, double theta) {
-    pr.ec = ellipse ? cos(theta) : 1.0;
-    pr.es = ellipse ? sin(theta) : 0.0;
-    pr.fc = (float)pr.ec;
-    pr.fs = (float)pr.es;
+    double c = 1.0, s = 0.0;
+    if (ellipse) sincos(theta, &s, &c);
+    pr.ec = c;
+    pr.es = s;
+    pr.fc = (float)c;
+    pr.fs = (float)s;
 }
 
 // Record of particle p from its state (X, A, theta) and constants (R, B,
@@ -260,7 +255,7 @@ __device__ void make_record_from(const InstDesc& in, int p, int D, const Shape& 
         at[d] = r.t;
         nt *= r.t.na + r.t.nb;
     }
-    record_radius(in, pr, R, B, nt);
+    record_radius(in, pr, in.rconst[p], nt);
     record_orientation(pr, B != R, theta);
     in.prec_out[p] = pr;
 }
@@ -321,34 +316,64 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
 // in the shuffles only): wall forces, the corrected position, and on the last
 // sub-step A^{n+1}, theta^{n+1}, U^{n-1} <- U^n and the record for the next
 // step.  Each lane evaluates the expressions of a serial loop over d.
+// The operands of update_lane, loaded in one batch before the pair search so
+// that their latency overlaps it.
+struct LaneIn {
+    double X0, Ub, Wn, Un, Wo, Th, invrhos, cw, idl, Ri, Bi, gfac, invc, Acor, ec, es;
+    int cnt;
+    RecConst rc;
+};
+
+__device__ __forceinline__ LaneIn load_lane(const InstDesc& in, int i, int d, bool valid, int src, int first) {
+    if (!valid) {  // in-range operands for the shuffle-only lanes
+        i = 0;
+        d = 0;
+    }
+    const long long j = 3LL * i + d;
+    LaneIn L;
+    L.X0 = in.Xk[(long long)src * in.np * 3 + j];
+    L.Ub = in.Ubar[j];
+    L.Wn = in.Wn[j];
+    L.Un = in.Un[j];
+    L.Wo = in.W[j];
+    L.Th = in.theta[j];
+    const double* pc = in.pconst + PCONST_N * i;
+    L.invrhos = pc[PC_INVRHOS];
+    L.cw = pc[PC_CWALL];
+    L.idl = pc[PC_INVDELTA];
+    L.Ri = pc[PC_R];
+    L.Bi = pc[PC_B];
+    L.gfac = pc[PC_GFAC];
+    L.invc = in.invc[i];
+    L.cnt = in.count[i];
+    L.Acor = first ? 0.0 : in.Acor[j];
+    L.ec = in.prec[i].ec;  // orientation theta^n of this step's record
+    L.es = in.prec[i].es;
+    L.rc = in.rconst[i];
+    return L;
+}
+
 __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid, const double* F1in,
                             const double* F2in, int src, double h, int first, int last, int D,
-                            const Shape& sh, AxisTiles* at) {
+                            const Shape& sh, AxisTiles* at, const LaneIn& L) {
     if (!valid) {  // in-range operands for the shuffle-only lanes; nothing is stored
         i = 0;
         d = 0;
     }
     const int dst = src ^ 1;
     const long long j = 3LL * i + d;
-    // every operand up front, in one batch of loads
-    const double X0 = in.Xk[(long long)src * in.np * 3 + j];
-    const double Ub = in.Ubar[j], Wn = in.Wn[j], Un = in.Un[j], Wo = in.W[j], Th = in.theta[j];
+    const double X0 = L.X0, Ub = L.Ub, Wn = L.Wn, Un = L.Un, Wo = L.Wo, Th = L.Th;
     double F1 = F1in[d], F2 = F2in[d];
-    const double* pc = in.pconst + PCONST_N * i;
-    const double invrhos = pc[PC_INVRHOS], cw = pc[PC_CWALL], idl = pc[PC_INVDELTA], Ri = pc[PC_R];
-    const double Bi = pc[PC_B];
-    const double gfac = pc[PC_GFAC];
-    const double invc = in.invc[i];
-    const int cnt = in.count[i];
+    const double invrhos = L.invrhos, cw = L.cw, idl = L.idl, Ri = L.Ri, Bi = L.Bi, gfac = L.gfac;
+    const double invc = L.invc;
+    const int cnt = L.cnt;
     const double invM = invrhos * invc;  // 1 / (rho_s n)
     const double Xst = fma(h, Ub, X0);
     // extent along axis d: the radius, or for an ellipse at theta^n (this
     // step's record) its support distance normal to the walls of axis d
     double Rd = Ri;
-    if (Bi != Ri && d < 2) {
-        const PRec& rn = in.prec[i];
-        Rd = d == 0 ? extent_along(Ri, Bi, rn.ec, rn.es, 1.0, 0.0) : extent_along(Ri, Bi, rn.ec, rn.es, 0.0, 1.0);
-    }
+    if (Bi != Ri && d < 2)
+        Rd = d == 0 ? extent_along(Ri, Bi, L.ec, L.es, 1.0, 0.0) : extent_along(Ri, Bi, L.ec, L.es, 0.0, 1.0);
     wall_force_d(in, d, X0, F1, cw, idl, Rd);
     wall_force_d(in, d, Xst, F2, cw, idl, Rd);
     const double c = 0.25 * h * h * invM;  // (1 / 2M) h^2 / 2
@@ -356,7 +381,7 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
     const double Xn = Xst + cor;
     // A^{n+1} = 2 (X^{n+1} - X^n - Ubar) is twice the sum of the corrections;
     // summed directly, since the difference of positions cancels catastrophically
-    const double acc = first ? cor : in.Acor[j] + cor;
+    const double acc = first ? cor : L.Acor + cor;
     const float Rf = (float)Ri;
     if (!last) {
         if (valid) {
@@ -413,7 +438,7 @@ __device__ void update_lane(const InstDesc& in, int i, int d, int sl, bool valid
         pr.frac[d] = r.frac;
         pr.a[d] = r.a;
         at[d] = r.t;
-        if (d == 0) record_radius(in, pr, Ri, Bi, nt);
+        if (d == 0) record_radius(in, pr, L.rc, nt);
         if (d == 2) record_orientation(pr, Bi != Ri, Tn);
     }
 }
@@ -471,7 +496,7 @@ __device__ bool grid_sync(GridBar* gb, int* status, unsigned long long limit_ns)
 // step's fluid kernel) into exact integer sums, and mark it empty again for
 // the next step.  The warps' totals are exact (integer reductions; 64-bit
 // sums by limbs) and so is their sum, so the totals do not depend on the order.
-constexpr int BS_THREADS = 256;
+constexpr int BS_THREADS = 128;  // 4 blocks per SM: 500 particles in one wave
 constexpr int BS_PER = 8;  // entries of a thread in flight at a time
 
 template <int D>
@@ -544,9 +569,10 @@ __device__ __forceinline__ void box_block_sums(const InstDesc& in, int p, long l
         for (int k = 0; k < NPV; ++k) red[warp][k] = v[k];
 }
 
-__global__ void __launch_bounds__(BS_THREADS) k_box_sums(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(BS_THREADS, 4) k_box_sums(const InstDesc* __restrict__ insts,
                                                        const PartRef* __restrict__ refs, int D) {
     __shared__ long long red[BS_THREADS / 32][NPV];
+    __shared__ long long tot[NPV];
     const PartRef r = refs[blockIdx.x];
     if (r.inst < 0) return;  // padding entry (block-uniform)
     const InstDesc& in = insts[r.inst];
@@ -557,28 +583,20 @@ __global__ void __launch_bounds__(BS_THREADS) k_box_sums(const InstDesc* __restr
         long long t = 0;
         for (int w = 0; w < BS_THREADS / 32; ++w) t += red[w][threadIdx.x];
         in.btot[(long long)r.p * NPV + threadIdx.x] = t;
+        tot[threadIdx.x] = t;
     }
-}
-
-// Phase 0: the rigid-body projection (Eq. 22) of the block's 8 particles from
-// their box totals; one thread per particle component does the FP64 part.
-__device__ void phase_finalize(const InstDesc& in, const PartRef* refs, int ntotal, int D, int gp0,
-                               long long (*tot)[NPV]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gp = gp0 + warp;
-    if (warp < PB && lane < NPV && gp < ntotal && refs[gp].inst >= 0)
-        tot[warp][lane] = __ldcg(in.btot + (long long)refs[gp].p * NPV + lane);
     __syncthreads();
-    // one lane per (particle, component): translation on warp 0, rotation on warp 1
-    const int sl = lane & (PB - 1), c = lane / PB;
-    if (warp < 2 && c < 3 && gp0 + sl < ntotal && refs[gp0 + sl].inst >= 0) {
-        const int p = refs[gp0 + sl].p;
+    // the second pass of Eq. 22 for this particle: translation on warp 0,
+    // rotation on warp 1, one lane per component; the kernel boundary after
+    // it is the grid-wide barrier Algorithm 1 needs (every particle's U^n)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < 3) {
         if (warp == 0) {
-            if (D == 2) finalize_translation<2>(in, p, tot[sl], c);
-            else finalize_translation<3>(in, p, tot[sl], c);
-        } else {
-            if (D == 2) finalize_rotation<2>(in, p, tot[sl], c);
-            else finalize_rotation<3>(in, p, tot[sl], c);
+            if (D == 2) finalize_translation<2>(in, r.p, tot, lane);
+            else finalize_translation<3>(in, r.p, tot, lane);
+        } else if (warp == 1) {
+            if (D == 2) finalize_rotation<2>(in, r.p, tot, lane);
+            else finalize_rotation<3>(in, r.p, tot, lane);
         }
     }
 }
@@ -605,6 +623,11 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
         cp = in.pconst[PCONST_N * i + PC_CPAIR];
         idl = in.pconst[PCONST_N * i + PC_INVDELTA];
     }
+    // warp 0: the operands of the update (one lane per particle component)
+    const int usl = lane & (PB - 1), ud = lane / PB;
+    const bool uvalid = warp == 0 && ud < 3 && gp0 + usl < ntotal && refs[gp0 + usl].inst >= 0;
+    LaneIn li;
+    if (warp == 0) li = load_lane(in, uvalid ? refs[gp0 + usl].p : 0, ud, uvalid, src, first);
     for (int j0 = 0; j0 < in.np; j0 += XCHUNK) {
         const int nj = min(XCHUNK, in.np - j0);
         __syncthreads();
@@ -625,24 +648,21 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
             }
     }
     __syncthreads();
-    if (warp == 0) {  // one lane per (particle, component)
-        const int sl = lane & (PB - 1), d = lane / PB;
-        const bool valid = d < 3 && gp0 + sl < ntotal && refs[gp0 + sl].inst >= 0;
-        update_lane(in, valid ? refs[gp0 + sl].p : 0, d, sl, valid, sF[sl], sF[sl] + 3, src, h, first, last, D, sh,
-                    sAT[sl]);
-    }
+    if (warp == 0)  // one lane per (particle, component)
+        update_lane(in, uvalid ? refs[gp0 + usl].p : 0, ud, usl, uvalid, sF[usl], sF[usl] + 3, src, h, first, last,
+                    D, sh, sAT[usl], li);
 }
 
 // Particle part of one time step for the block's 8 particles (one instance),
-// phases first..last: 0 = projection, k = sub-step k of Algorithm 1; after the
-// last sub-step the warps append their particle to the next step's tile
-// lists.  With more than one phase the blocks meet at grid barriers between
-// phases (the launch guarantees they are all resident).
-__global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ insts,
+// phases first..last, phase k = sub-step k of Algorithm 1 (the projection of
+// Eq. 22 ran in k_box_sums); after the last sub-step the warps append their
+// particle to the next step's tile lists.  With more than one phase (K > 1)
+// the blocks meet at grid barriers between phases (the launch guarantees they
+// are all resident); with K = 1 there is no barrier.
+__global__ void __launch_bounds__(256, 1) k_particles(const InstDesc* __restrict__ insts,
                                                    const PartRef* __restrict__ refs, int ntotal,
                                                    int D, int K, int first, int last, int lpar,
                                                    Shape sh, GridBar* gb, unsigned long long wait_ns) {
-    __shared__ long long tot[PB][NPV];
     __shared__ double sF[PB][6];
     __shared__ AxisTiles sAT[PB][3];
     __shared__ float4 xs[XCHUNK];
@@ -653,8 +673,7 @@ __global__ void __launch_bounds__(256) k_particles(const InstDesc* __restrict__ 
     const InstDesc& in = sdesc;
     for (int ph = first; ph <= last; ++ph) {
         if (ph > first && !grid_sync(gb, in.status, wait_ns)) return;
-        if (ph == 0) phase_finalize(in, refs, ntotal, D, gp0, tot);
-        else phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == 1, ph == K, sh, xs, xs2, sF, sAT);
+        phase_substep(in, refs, ntotal, D, gp0, (ph - 1) & 1, K, ph == 1, ph == K, sh, xs, xs2, sF, sAT);
     }
     if (last == K) {
         __syncthreads();  // records and tile ranges of the block's particles are ready
@@ -691,11 +710,11 @@ cudaError_t launch_particles(const InstDesc* insts, const PartRef* refs, int nto
                              long long wait_ns) {
     const int blocks = (ntotal + PB - 1) / PB;
     const unsigned long long lim = wait_ns < 0 ? PWAIT_NS : (unsigned long long)wait_ns;
-    if (fused) {
-        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, 0, K, lpar, sh, gb, lim);
+    if (fused || K == 1) {
+        k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, 1, K, lpar, sh, gb, lim);
         return cudaGetLastError();
     }
-    for (int ph = 0; ph <= K; ++ph)
+    for (int ph = 1; ph <= K; ++ph)
         k_particles<<<blocks, 256, 0, st>>>(insts, refs, ntotal, D, K, ph, ph, lpar, sh, gb, lim);
     return cudaGetLastError();
 }

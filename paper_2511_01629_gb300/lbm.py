@@ -118,6 +118,7 @@ def lib():
         "lbm_launches_per_step": (C.c_int, [_vp]),
         "lbm_set_particle_wait_limit": (C.c_int, [_vp, C.c_double]),
         "lbm_fluid_step_only": (C.c_int, [_vp]),
+        "lbm_step_timed": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
         "lbm_steps_done": (C.c_longlong, [_vp]),
         "lbm_total_nodes": (C.c_longlong, [_vp]),
         "lbm_adjoint_forward": (C.c_int, [_vp, C.c_int, C.c_int]),
@@ -358,6 +359,13 @@ class LBM:
 
     def fluid_step_only(self):
         self._check(lib().lbm_fluid_step_only(self._h))
+
+    def step_timed(self, n):
+        """n steps launched one by one with CUDA events around each kernel:
+        mean ms per step of (fluid kernel, box sums, particle kernel)."""
+        t = (C.c_float * 3)()
+        self._check(lib().lbm_step_timed(self._h, int(n), C.byref(t, 0), C.byref(t, 4), C.byref(t, 8)))
+        return float(t[0]), float(t[1]), float(t[2])
 
     # -- adjoint --
     def adjoint_forward(self, nsteps: int, seg_len: int = 0):

@@ -2,9 +2,10 @@
 
 A bounded wait that runs out must be reported by lbm_sync as LBM_ERR_TIMEOUT,
 after which the context refuses work with LBM_ERR_STATE while the device
-stays usable.  The particle kernel's grid barrier is made to run out by a
-zero wait bound (lbm_set_particle_wait_limit): the first block to arrive at
-the barrier never finds it open on its first look.  The waits stay bounded
+stays usable.  The particle kernel's grid barrier (between the sub-steps of
+Algorithm 1, so K = 2) is made to run out by a zero wait bound
+(lbm_set_particle_wait_limit): the first block to arrive at the barrier
+never finds it open on its first look.  The waits stay bounded
 throughout and that kernel issues no asynchronous copies, so nothing is left
 in flight when it returns.
 """
@@ -27,8 +28,11 @@ def _gpu_setup():
 
 
 def _workload():
-    # 64 disks: eight particle blocks, so the step's barrier spans several blocks
-    return W.many_disks(seed=2, nx=384, ny=768, count=64)
+    # 64 disks: eight particle blocks, so the barrier between the two
+    # sub-steps spans several blocks
+    w = W.many_disks(seed=2, nx=384, ny=768, count=64)
+    w.K = 2
+    return w
 
 
 @gpu
