@@ -576,6 +576,13 @@ __global__ void __launch_bounds__(BS_THREADS, 4) k_box_sums(const InstDesc* __re
     const PartRef r = refs[blockIdx.x];
     if (r.inst < 0) return;  // padding entry (block-uniform)
     const InstDesc& in = insts[r.inst];
+    if (threadIdx.x >= BS_THREADS - 4) {  // warm L1 with what the second pass reads
+        const int k = threadIdx.x - (BS_THREADS - 4);
+        const char* a = k < 2 ? reinterpret_cast<const char*>(in.prec + r.p) + 128 * k
+                              : (k == 2 ? reinterpret_cast<const char*>(in.U + 3 * r.p)
+                                        : reinterpret_cast<const char*>(in.pconst + PCONST_N * r.p));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+    }
     if (D == 2) box_block_sums<2>(in, r.p, red);
     else box_block_sums<3>(in, r.p, red);
     __syncthreads();
@@ -630,10 +637,25 @@ __device__ void phase_substep(const InstDesc& in, const PartRef* refs, int ntota
     if (warp == 0) li = load_lane(in, uvalid ? refs[gp0 + usl].p : 0, ud, uvalid, src, first);
     for (int j0 = 0; j0 < in.np; j0 += XCHUNK) {
         const int nj = min(XCHUNK, in.np - j0);
+        // every load of the chunk in flight at once, then the shared stores
+        constexpr int PER = XCHUNK / 256;  // blockDim.x == 256
+        float4 ra[PER], rb[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + 256 * u;
+            if (k < nj) {
+                ra[u] = Xfb[j0 + k];
+                rb[u] = Xsb[j0 + k];
+            }
+        }
         __syncthreads();
-        for (int k = threadIdx.x; k < nj; k += blockDim.x) {
-            xs[k] = Xfb[j0 + k];
-            xs2[k] = Xsb[j0 + k];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int k = threadIdx.x + 256 * u;
+            if (k < nj) {
+                xs[k] = ra[u];
+                xs2[k] = rb[u];
+            }
         }
         __syncthreads();
         if (mine) pair_chunk(in, i, src, h, lane, xs, xs2, j0, nj, xi, xi2, cp, idl, f1, f2);
