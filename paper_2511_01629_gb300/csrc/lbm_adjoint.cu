@@ -292,83 +292,98 @@ __global__ void __launch_bounds__(256, Q == 9 ? 3 : 2) k_adj_fluid(const InstDes
         if (y >= ny || z >= nz) continue;  // warp-uniform
         const bool row_in = y >= 1 && y + 1 < ny && (D == 2 || (z >= 1 && z + 1 < nz));
         const int rowoff = (z * ny + y) * pitch;
-        for (int xo = lane; xo < wpad; xo += 32) {
-            const int x = x0 + xo;
-            const bool valid = xo < w;
-            const int xs = valid ? x : x0;  // lanes beyond the row compute on a valid node, store nothing
-            const int node = rowoff + xs;
-            // warp-uniform: every lane's stencil stays inside the box
-            const bool interior = __all_sync(0xffffffffu, row_in && xs >= 1 && xs + 1 < nx);
-            float f[QS], lam[QS];
-            if (interior) {
+        // D2Q9: two nodes per lane (xo0 and xo0 + 32), both nodes' gathers in
+        // flight together before either is computed (D3Q19: one, registers)
+        constexpr int NPL = Q == 9 ? 2 : 1;
+        for (int xo0 = lane; xo0 < wpad; xo0 += 32 * NPL) {
+            float f[NPL][QS], lam[NPL][QS];
+            int xsv[NPL], nodev[NPL];
+            bool validv[NPL];
 #pragma unroll
-                for (int q = 0; q < QS; ++q)
-                    f[q] = VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (node + offF[q]), sl);
-            } else {
-                PullAll<Q, S, 1>::pre(in, fin, xs, y, z, qs, f);
-            }
-            if (lam_mode == 0) {
+            for (int h = 0; h < NPL; ++h) {
+                const int xo = xo0 + 32 * h;
+                validv[h] = xo < w;
+                const int xs = validv[h] ? x0 + xo : x0;  // lanes beyond the row compute on a valid node, store nothing
+                xsv[h] = xs;
+                const int node = rowoff + xs;
+                nodev[h] = node;
+                // warp-uniform: every lane's stencil stays inside the box
+                const bool interior = __all_sync(0xffffffffu, row_in && xs >= 1 && xs + 1 < nx);
                 if (interior) {
 #pragma unroll
-                    for (int q = 0; q < QS; ++q) lam[q] = __ldg(lsrc + (node + offL[q]));
+                    for (int q = 0; q < QS; ++q)
+                        f[h][q] = VecIO<S, 1 + (sizeof(S) == 2)>::load1(fin + (node + offF[q]), sl);
                 } else {
-                    PullAll<Q, S, 1>::lam(in, lsrc, xs, y, z, qs, lam);
+                    PullAll<Q, S, 1>::pre(in, fin, xs, y, z, qs, f[h]);
                 }
-            } else if (lam_mode == 1) {
-                const long long nd = ((long long)z * ny + y) * nx + xs;
+                if (lam_mode == 0) {
+                    if (interior) {
 #pragma unroll
-                for (int q = 1; q < Q; ++q) lam[q - 1] = __ldg(lsrc + (long long)q * N + nd);
-            } else {
+                        for (int q = 0; q < QS; ++q) lam[h][q] = __ldg(lsrc + (node + offL[q]));
+                    } else {
+                        PullAll<Q, S, 1>::lam(in, lsrc, xs, y, z, qs, lam[h]);
+                    }
+                } else if (lam_mode == 1) {
+                    const long long nd = ((long long)z * ny + y) * nx + xs;
 #pragma unroll
-                for (int q = 0; q < QS; ++q) lam[q] = 0.f;
-            }
-            float a[3] = {gd[0], gd[1], gd[2]};
-            float ubp[3] = {0.f, 0.f, 0.f};
-            int own = -1;
-            if (ncand > 0) {
-                const int xyz[3] = {xs, y, z};
-                int slt = -1;
-                own = owner_of<D>(geo, cand, ncand, xyz, &slt);
-                if (own >= 0) {
-                    const Cand& cd = cand[slt];
-                    float rr[3] = {0.f, 0.f, 0.f};
+                    for (int q = 1; q < Q; ++q) lam[h][q - 1] = __ldg(lsrc + (long long)q * N + nd);
+                } else {
 #pragma unroll
-                    for (int d = 0; d < D; ++d)
-                        rr[d] = (float)wrap_int(xyz[d] - cd.ref[d], in.n[d], in.periodic[d]) - cd.frac[d];
-                    const float* cf = af.coef + 8LL * own;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) a[d] += cd.a[d];
-                    // d U / d u = 1 / count, d W / d u: (I^-1 dW) x r
-                    ubp[0] = cf[0] + (cf[4] * rr[2] - cf[5] * rr[1]);
-                    ubp[1] = cf[1] + (cf[5] * rr[0] - cf[3] * rr[2]);
-                    ubp[2] = D == 3 ? cf[2] + (cf[3] * rr[1] - cf[4] * rr[0]) : 0.f;
+                    for (int q = 0; q < QS; ++q) lam[h][q] = 0.f;
                 }
-                if (!valid) own = -1;
             }
-            float fb[QS], ab[3], alb;
-            const bool any_solid = __any_sync(0xffffffffu, own >= 0);
-            node_adjoint<Q>(f, a, lam, own >= 0, any_solid, ubp, ck, fb, ab, &alb);
-            if (valid) {
 #pragma unroll
-                for (int q = 0; q < QS; ++q) ldst[node + q * qs] = fb[q];
-            }
-            // per-particle sums of the adjoint acceleration and alpha derivative
-            unsigned pend = __ballot_sync(0xffffffffu, own >= 0);
-            while (pend) {
-                const int leader = __ffs(pend) - 1;
-                const int p = __shfl_sync(0xffffffffu, own, leader);
-                const bool mine = own == p;
-                float v[4] = {mine ? ab[0] : 0.f, mine ? ab[1] : 0.f, mine ? ab[2] : 0.f, mine ? alb : 0.f};
+            for (int h = 0; h < NPL; ++h) {
+                const int xs = xsv[h], node = nodev[h];
+                const bool valid = validv[h];
+                float a[3] = {gd[0], gd[1], gd[2]};
+                float ubp[3] = {0.f, 0.f, 0.f};
+                int own = -1;
+                if (ncand > 0) {
+                    const int xyz[3] = {xs, y, z};
+                    int slt = -1;
+                    own = owner_of<D>(geo, cand, ncand, xyz, &slt);
+                    if (own >= 0) {
+                        const Cand& cd = cand[slt];
+                        float rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                        for (int d = 0; d < D; ++d)
+                            rr[d] = (float)wrap_int(xyz[d] - cd.ref[d], in.n[d], in.periodic[d]) - cd.frac[d];
+                        const float* cf = af.coef + 8LL * own;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-                if (lane == leader) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < D || k == 3) atomicAdd(af.Abar + 4LL * p + k, (double)v[k]);
+                        for (int d = 0; d < 3; ++d) a[d] += cd.a[d];
+                        // d U / d u = 1 / count, d W / d u: (I^-1 dW) x r
+                        ubp[0] = cf[0] + (cf[4] * rr[2] - cf[5] * rr[1]);
+                        ubp[1] = cf[1] + (cf[5] * rr[0] - cf[3] * rr[2]);
+                        ubp[2] = D == 3 ? cf[2] + (cf[3] * rr[1] - cf[4] * rr[0]) : 0.f;
+                    }
+                    if (!valid) own = -1;
                 }
-                pend &= ~__ballot_sync(0xffffffffu, mine);
+                float fb[QS], ab[3], alb;
+                const bool any_solid = __any_sync(0xffffffffu, own >= 0);
+                node_adjoint<Q>(f[h], a, lam[h], own >= 0, any_solid, ubp, ck, fb, ab, &alb);
+                if (valid) {
+#pragma unroll
+                    for (int q = 0; q < QS; ++q) ldst[node + q * qs] = fb[q];
+                }
+                // per-particle sums of the adjoint acceleration and alpha derivative
+                unsigned pend = __ballot_sync(0xffffffffu, own >= 0);
+                while (pend) {
+                    const int leader = __ffs(pend) - 1;
+                    const int p = __shfl_sync(0xffffffffu, own, leader);
+                    const bool mine = own == p;
+                    float v[4] = {mine ? ab[0] : 0.f, mine ? ab[1] : 0.f, mine ? ab[2] : 0.f, mine ? alb : 0.f};
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+                    if (lane == leader) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < D || k == 3) atomicAdd(af.Abar + 4LL * p + k, (double)v[k]);
+                    }
+                    pend &= ~__ballot_sync(0xffffffffu, mine);
+                }
             }
         }
     }
