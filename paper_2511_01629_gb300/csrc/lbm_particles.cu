@@ -49,16 +49,24 @@ __device__ void pair_chunk(const InstDesc& in, int i, int src, double h, int lan
         const int j = j0 + jj;
         if (j == i) continue;
         bool near[2];
+        bool far = false;
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1 && far) break;
             const float4 a = pass ? xi2 : xi, b = pass ? xs2[jj] : xs[jj];
             float dv[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (per[d]) dv[d] -= nf[d] * rintf(dv[d] / nf[d]);
             const float lim = reach + b.w;
-            near[pass] = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] <= lim * lim;
+            const float d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+            near[pass] = d2 <= lim * lim;
+            // a predicted position lies within |h Ubar| < sqrt(3)/2 of X^n (a larger
+            // step is reported as ST_DISPLACEMENT), so a pair more than 2 beyond
+            // range at X^n is out of range at both position sets
+            if (pass == 0) far = d2 > (lim + 2.0f) * (lim + 2.0f);
         }
+        if (far) continue;
         if (!near[0] && !near[1]) continue;
         const double Bi = in.pconst[PCONST_N * i + PC_B], Bj = in.pconst[PCONST_N * j + PC_B];
         const bool ell = Bi != in.R[i] || Bj != in.R[j];
