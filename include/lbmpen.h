@@ -10,12 +10,15 @@
  *      the penalization source S = w/(2 cs^4) alpha Pi_neq : (c c - cs^2 I)
  *      (Eq. 17);
  *   5. per-particle rigid-body projection U, omega over each solid domain
- *      (Eq. 22) from in-kernel partial sums, reduced in a fixed order;
+ *      (Eq. 22): the fused kernel stores each solid node's velocity in its
+ *      particle's velocity box, and exact integer sums over the box give
+ *      U and omega, independent of the order of summation;
  *   6. particle update: repulsive collision forces (Eqs. 19-21) and the
  *      predictor-corrector of Algorithm 1, which also yields the collision
  *      acceleration A applied on the particle's nodes in the next step.
- * Steps 1-5 run in one fused CUDA kernel per step over all instances; step 6
- * runs in FP64 in small per-particle kernels.
+ * Steps 1-4 and the box stores run in one fused CUDA kernel per step over all
+ * instances; the sums and the second pass of step 5 in one block per
+ * particle; step 6 in FP64 in one more kernel.
  *
  * Units: lattice units, dx = dt = 1 (Sec. 3 preamble).  Node (i, j, k) sits at
  * integer coordinates; fields are row-major with x fastest.

@@ -40,10 +40,19 @@ CASES = {
     "mixed": dict(n=(150, 90, 1), periodic=(1, 0, 1),
                   pos=[[30.4, 45.2], [75.1, 40.7], [118.6, 52.3]], a=[12.0, 9.0, 10.5],
                   b=[4.0, 9.0, 7.25], theta=[-0.4, 0.0, 2.2], ratio=[1.5, 1.2, 1.8]),
-    # a thin ellipse near a wall: the wall force acts on its support distance
+    # a thin ellipse near a wall
     "wall": dict(n=(64, 96, 1), periodic=(0, 0, 1), pos=[[5.4, 50.3]], a=[15.0], b=[3.0],
                  theta=[1.35], ratio=[1.4], g=(-4e-4, -1e-4, 0.0)),
+    # the same ellipse within the wall's range from the first step: the wall force acts on
+    # its support distance normal to the wall (4.40), not on its semi-major axis
+    "wall-contact": dict(n=(64, 96, 1), periodic=(0, 0, 1), pos=[[4.2, 50.3]], a=[15.0], b=[3.0],
+                         theta=[1.35], ratio=[1.4], g=(-4e-4, -1e-4, 0.0)),
+    # two tilted ellipses 0.5 apart along their line of centres (angle 0.3), inside the pair
+    # range delta = 1 from the first step, with K = 2 sub-steps (the grid barrier path)
+    "pair-contact": dict(n=(110, 100, 1), periodic=(0, 0, 1), pos=[[45.3, 48.1], [63.1423, 53.6193]],
+                         a=[12.0, 12.0], b=[5.0, 5.0], theta=[0.5, -0.9], ratio=[1.5, 1.3], K=2),
 }
+CONTACT = ("wall-contact", "pair-contact")
 
 
 @gpu
@@ -72,6 +81,10 @@ def test_ellipses_match_oracle(name, storage):
         assert cp["dU"] <= tol * cp["Uscale"] + 1e-12, cp
         assert cp["dX"] < (1e-6 if storage == lbm.LBM_FP32 else 1e-3), cp
         assert th < (1e-7 if storage == lbm.LBM_FP32 else 1e-4)
+        if name in CONTACT:  # the collision acceleration A^{n+1} of Algorithm 1
+            aref = np.abs(ref.particles()["A"]).max()
+            assert aref > 0
+            assert cp["dA"] <= (1e-6 if storage == lbm.LBM_FP32 else 1e-3) * aref, (cp, aref)
     # the ellipses did turn
     assert np.abs(ref.particles()["theta"][:, 2] - np.asarray(w.theta)).max() > 2e-5
     sim.close()
