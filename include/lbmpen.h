@@ -176,6 +176,15 @@ int lbm_get_fields(lbm_ctx* ctx, int instance, float* u, float* p, int* owner, i
  * synchronises): pos X^{n+1} (n*D), vel U^n (n*D), omega omega^n (n or n*3),
  * theta orientation (n or n*3; trapezoidal integral of omega), accel A^{n+1}
  * (n*D), count = solid nodes at step n (n). */
+/* The same state copied asynchronously on the context stream, without
+ * synchronising: each non-NULL array receives n*3 values (x, y, z; z = 0 in 2D;
+ * omega and theta carry their z component in 2D) and count n values.  The
+ * copies run after the steps already enqueued; the arrays hold the state
+ * once the stream has reached them (lbm_sync, or any later synchronising
+ * call).  With page-locked (pinned) host memory the call returns at once;
+ * the arrays must stay valid until then. */
+int lbm_get_particles_async(lbm_ctx* ctx, int instance, double* pos3, double* vel3, double* omega3,
+                            double* theta3, double* accel3, int* count);
 int lbm_get_particles(lbm_ctx* ctx, int instance, double* pos, double* vel, double* omega,
                       double* theta, double* accel, int* count);
 int lbm_num_particles(const lbm_ctx* ctx, int instance);

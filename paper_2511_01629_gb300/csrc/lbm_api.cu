@@ -1040,6 +1040,22 @@ int lbm_get_particles(lbm_ctx* ctx, int i, double* pos, double* vel, double* ome
     return LBM_OK;
 }
 
+int lbm_get_particles_async(lbm_ctx* ctx, int i, double* pos3, double* vel3, double* omega3, double* theta3,
+                            double* accel3, int* count) {
+    int rc = check_inst(ctx, i);
+    if (rc) return rc;
+    Instance& I = ctx->inst[i];
+    const int n = I.np;
+    if (n == 0) return LBM_OK;
+    const size_t b3 = sizeof(double) * 3 * n;
+    const std::pair<double*, DevBuf*> v3[] = {{pos3, &I.X}, {vel3, &I.U}, {omega3, &I.W}, {theta3, &I.theta},
+                                              {accel3, &I.A}};
+    for (const auto& c : v3)
+        if (c.first) CK(cudaMemcpyAsync(c.first, c.second->ptr, b3, cudaMemcpyDeviceToHost, ctx->st));
+    if (count) CK(cudaMemcpyAsync(count, I.count.ptr, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->st));
+    return LBM_OK;
+}
+
 int lbm_set_populations(lbm_ctx* ctx, int i, const float* f, int on_device) {
     int rc = check_inst(ctx, i);
     if (rc) return rc;

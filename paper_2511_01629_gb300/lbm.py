@@ -119,6 +119,7 @@ def lib():
         "lbm_set_particle_wait_limit": (C.c_int, [_vp, C.c_double]),
         "lbm_fluid_step_only": (C.c_int, [_vp]),
         "lbm_step_timed": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+        "lbm_get_particles_async": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lbm_steps_done": (C.c_longlong, [_vp]),
         "lbm_total_nodes": (C.c_longlong, [_vp]),
         "lbm_adjoint_forward": (C.c_int, [_vp, C.c_int, C.c_int]),
@@ -359,6 +360,16 @@ class LBM:
 
     def fluid_step_only(self):
         self._check(lib().lbm_fluid_step_only(self._h))
+
+    def particles_async(self, out, i=0):
+        """Enqueue the copy of instance i's particle state into `out` (a dict
+        with any of X, U, W, theta, A as float64 [n, 3] arrays and count as int32
+        [n], contiguous, ideally in pinned memory) without synchronising; the
+        values are there after the next sync."""
+        p = {k: (None if out.get(k) is None else out[k].ctypes.data_as(C.c_void_p))
+             for k in ("X", "U", "W", "theta", "A", "count")}
+        self._check(lib().lbm_get_particles_async(self._h, i, p["X"], p["U"], p["W"], p["theta"], p["A"],
+                                                  p["count"]))
 
     def step_timed(self, n):
         """n steps launched one by one with CUDA events around each kernel:
