@@ -202,3 +202,17 @@ def test_rigid_rotation_inside_an_ellipse_is_recovered():
     assert cnt[0] > 0
     assert np.abs(U[0]).max() < 1e-18
     assert Wv[0, 2] == pytest.approx(Om, rel=1e-14)
+
+
+def test_bad_ellipses_are_refused():
+    """Axes out of order or non-positive, and ellipses in 3D, are refused by the
+    oracle (the C ABI refuses the same, tests/test_gpu_ellipse.py)."""
+    s = _sim()
+    with pytest.raises(ValueError):
+        s.add_ellipses([[40.0, 40.0]], [5.0], [6.0], [0.0], [1.2])  # b > a
+    with pytest.raises(ValueError):
+        s.add_ellipses([[40.0, 40.0]], [5.0], [0.0], [0.0], [1.2])  # b = 0
+    assert s.np == 0
+    s3 = oracle.Sim(oracle.make_config(D=3, n=(20, 20, 20), periodic=(0, 0, 0)))
+    with pytest.raises(ValueError):
+        s3.add_ellipses([[10.0, 10.0, 10.0]], [5.0], [3.0], [0.0], [1.2])
