@@ -221,7 +221,7 @@ int max_slots(const Instance& I, int D, const Shape& sh) {
         const int span = (int)ceil(2 * I.cfg.max_radius) + 4;
         k *= std::min(span / T[d] + 3, I.ntile[d]);  // a wrapped interval splits in two
     }
-    return std::min(std::max(k, 1), MAXK);
+    return std::max(k, 1);
 }
 
 InstDesc make_desc(lbm_ctx* ctx, const Instance& I) {

@@ -310,7 +310,9 @@ __device__ void append_tiles(const InstDesc& in, int p, const AxisTiles* at, int
         const int local = (tc[2] * in.ntile[1] + tc[1]) * in.ntile[0] + tc[0];
         const int pos = atomicAdd(&in.list_cnt[lpar][local], 1);
         if (pos < LIST_CAP) {
-            in.list_ent[lpar][(long long)local * LIST_CAP + pos] = ((uint32_t)p << KBITS) | (uint32_t)k;
+            // the slot is informational (a particle may cover more than MAXK
+            // tiles): only its low KBITS bits go into the entry, below p
+            in.list_ent[lpar][(long long)local * LIST_CAP + pos] = ((uint32_t)p << KBITS) | (uint32_t)(k & (MAXK - 1));
             cd.k = k;
             rec[(long long)local * LIST_CAP + pos] = cd;
         } else {
