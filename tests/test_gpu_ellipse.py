@@ -51,6 +51,10 @@ CASES = {
     # range delta = 1 from the first step, with K = 2 sub-steps (the grid barrier path)
     "pair-contact": dict(n=(110, 100, 1), periodic=(0, 0, 1), pos=[[45.3, 48.1], [63.1423, 53.6193]],
                          a=[12.0, 12.0], b=[5.0, 5.0], theta=[0.5, -0.9], ratio=[1.5, 1.3], K=2),
+    # the longest and thinnest: a = 120 (the 2D maximum), b = 1.5, aspect 80; the float
+    # filter's band widens with a / b, and a 245 x 245 velocity box
+    "needle": dict(n=(300, 260, 1), periodic=(0, 0, 1), pos=[[150.2, 130.3]], a=[120.0], b=[1.5],
+                   theta=[0.37], ratio=[1.3]),
 }
 CONTACT = ("wall-contact", "pair-contact")
 
@@ -85,8 +89,8 @@ def test_ellipses_match_oracle(name, storage):
             aref = np.abs(ref.particles()["A"]).max()
             assert aref > 0
             assert cp["dA"] <= (1e-6 if storage == lbm.LBM_FP32 else 1e-3) * aref, (cp, aref)
-    # the ellipses did turn
-    assert np.abs(ref.particles()["theta"][:, 2] - np.asarray(w.theta)).max() > 2e-5
+    # the ellipses did turn (the needle, long and light, turns slowly)
+    assert np.abs(ref.particles()["theta"][:, 2] - np.asarray(w.theta)).max() > (0 if name == "needle" else 2e-5)
     sim.close()
 
 
