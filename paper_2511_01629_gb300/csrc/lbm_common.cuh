@@ -244,28 +244,27 @@ __device__ __forceinline__ int owner_of(const Geo& in, const Cand* cand, int nca
 // Candidates whose solid domain can reach the row segment of width nodes
 // starting at x0 of row (y, z): a uniform test per candidate instead of a test per
 // node.  Bit c set = candidate c may own a node of the segment (ncand <= 32).
+// Lane c of the (converged) warp tests candidate c; a ballot gathers the bits.
 template <int D>
 __device__ __forceinline__ unsigned segment_candidates(const Geo& g, const Cand* cand, int ncand, int x0,
-                                                       int y, int z, int width = 32) {
-    unsigned act = 0;
-    for (int c = 0; c < ncand; ++c) {
-        const Cand& cd = cand[c];
+                                                       int y, int z, int width, int lane) {
+    bool live = false;
+    if (lane < ncand) {
+        const Cand& cd = cand[lane];
         const float dy = (float)wrap_int(y - cd.ref[1], g.n[1], g.per[1]) - cd.frac[1];
         float rest = cd.R2hi - dy * dy;
         if (D == 3) {
             const float dz = (float)wrap_int(z - cd.ref[2], g.n[2], g.per[2]) - cd.frac[2];
             rest -= dz * dz;
         }
-        if (rest < 0.f) continue;
-        const float hw = sqrtf(rest) + 1.0f;
-        // nearest distance along x from the centre to the segment [x0, x0 + width - 1]
-        const float dx0 = (float)wrap_int(x0 - cd.ref[0], g.n[0], g.per[0]) - cd.frac[0];
-        if (dx0 > hw || dx0 + (float)(width - 1) < -hw) {
-            if (!g.per[0]) continue;
+        if (rest >= 0.f) {
+            const float hw = sqrtf(rest) + 1.0f;
+            // nearest distance along x from the centre to the segment [x0, x0 + width - 1]
+            const float dx0 = (float)wrap_int(x0 - cd.ref[0], g.n[0], g.per[0]) - cd.frac[0];
+            live = g.per[0] || !(dx0 > hw || dx0 + (float)(width - 1) < -hw);
         }
-        act |= 1u << c;
     }
-    return act;
+    return __ballot_sync(0xffffffffu, live);
 }
 
 // Owner among the segment's live candidates (bit mask from segment_candidates).

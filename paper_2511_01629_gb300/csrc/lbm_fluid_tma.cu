@@ -251,9 +251,11 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
     constexpr int D = L::D;
     constexpr int QS = Q - 1;
     constexpr int H = 16 / (int)sizeof(S);
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // Base of the ring rounded up to 128 bytes by an offset from the shared
+    // array itself: a pointer rebuilt from an integer would lose its address
+    // space, and every access through it would become a generic load.
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     constexpr int rows = ROWS;  // == sh.ty * sh.tz
     constexpr int BW = TW + 2 * H;
     // elements between populations in a stage, and the row offset of population
@@ -582,7 +584,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                     own0 = owner_of<D>(geo, cand, ncand, xyz0, &sl0);
                     own1 = owner_of<D>(geo, cand, ncand, xyz1, &sl1);
                 } else if (ncand > 0) {
-                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 64, y, z, 64);
+                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 64, y, z, 64, lane);
                     if (act) {
                         own0 = owner_masked<D>(geo, cand, act, xyz0, &sl0);
                         own1 = owner_masked<D>(geo, cand, act, xyz1, &sl1);
