@@ -589,6 +589,52 @@ __device__ __forceinline__ void collide2(float2* f, const float2* a, bool solid0
     }
 }
 
+// FP16 storage at tau = 1: f holds the populations at the storage scale
+// (2^14 f, as read, without the 2^-14 multiply), and ks is CollK with A, fA
+// and sA multiplied by 2^14, so f* comes out at the storage scale too.  The
+// moments are linear sums, scaled to lattice units once (sload = 2^-14), and
+// a power-of-two scaling commutes with every rounding in the normal range,
+// so the stored halves are the same bits as those of collide2 followed by
+// the 2^14 multiply; this saves two multiplies per population and node.
+template <int Q>
+__device__ __forceinline__ void collide2_t1_scaled(float2* f, const float2* a, bool solid0, bool solid1,
+                                                   const CollK& ks, float sload, float2* u_out, float2* p_out) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    constexpr float inv_sa = (float)(1.0 / L::SUMA);
+    constexpr float kuu = (float)(1.5 - 0.5 * L::SUMA);
+    float2 s, m[3];
+    moments2<Q>(f, s, m);
+    s = mul2(s, bc2(sload));
+    m[0] = mul2(m[0], bc2(sload));
+    m[1] = mul2(m[1], bc2(sload));
+    if (D == 3) m[2] = mul2(m[2], bc2(sload));
+    float2 u[3];
+    u[0] = fma2(bc2(0.5f), a[0], m[0]);  // Eq. 15a
+    u[1] = fma2(bc2(0.5f), a[1], m[1]);
+    u[2] = D == 3 ? fma2(bc2(0.5f), a[2], m[2]) : bc2(0.f);
+    const float2 uu = D == 3 ? fma2(u[2], u[2], fma2(u[1], u[1], mul2(u[0], u[0])))
+                             : fma2(u[1], u[1], mul2(u[0], u[0]));
+    const float2 p = mul2(fma2(bc2(-kuu), uu, s), bc2(inv_sa));  // Eq. 15b
+    const float2 ua = D == 3 ? fma2(u[2], a[2], fma2(u[1], a[1], mul2(u[0], a[0])))
+                             : fma2(u[1], a[1], mul2(u[0], a[0]));
+    const float2 nua = mul2(ua, bc2(-1.0f));
+    const float2 base = fma2(bc2(-0.5f), uu, p);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u_out[d] = u[d];
+    *p_out = p;
+    if (solid0 || solid1) {  // Pi_neq of the populations in lattice units
+#pragma unroll
+        for (int q = 0; q < Q - 1; ++q) f[q] = mul2(f[q], bc2(sload));
+        float2 P[6];
+        pi_neq2<Q>(f, u, base, P);
+        const float2 trP = mul2(add2(add2(P[0], P[1]), P[2]), bc2(1.0f / 3.0f));
+        collide_pair2_t1<Q, 1, true>(f, u, a, base, nua, ks, P, trP, solid0, solid1);
+    } else {
+        collide_pair2_t1<Q, 1, false>(f, u, a, base, nua, ks, nullptr, bc2(0.f), false, false);
+    }
+}
+
 // One node (both halves of the packed arithmetic carry it): the same bits
 // as collide2 gives that node.
 template <int Q>

@@ -25,6 +25,8 @@
 // returns.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "lbm_common.cuh"
 
 namespace lbmpen {
@@ -514,6 +516,20 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         const int ex = h.ex, ecx = h.ecx;
         const float* ev = edgev + s * rows * QE;
         bool bad = false;
+        const float sstore_t = h.ti.sstore;
+        // FOLD (D2Q9, FP16 storage at tau = 1): the populations stay at the
+        // storage scale from the stage to the store (collide2_t1_scaled)
+        auto tile_rows = [&](auto fold_tag) {
+        constexpr bool FOLD = decltype(fold_tag)::value;
+        CollK cks = ck;
+        if constexpr (FOLD) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                cks.A[i] *= sstore_t;
+                cks.fA[i] *= sstore_t;
+                cks.sA[i] *= sstore_t;
+            }
+        }
         for (int r = cw; r < rows; r += nc) {
             const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
             if (y >= ny || z >= nz) continue;
@@ -539,8 +555,13 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
 #pragma unroll
                     for (int q = 1; q < Q; ++q) {
                         const S* src = rowbase + qoff(q) + lx - L::c(q, 0);
-                        if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, sload);
-                        else f[q - 1] = make_float2(to_float_scaled(src[0], sload), to_float_scaled(src[1], sload));
+                        if constexpr (FOLD) {
+                            if (L::c(q, 0) == 0) f[q - 1] = __half22float2(*reinterpret_cast<const __half2*>(src));
+                            else f[q - 1] = make_float2(__half2float(src[0]), __half2float(src[1]));
+                        } else {
+                            if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, sload);
+                            else f[q - 1] = make_float2(to_float_scaled(src[0], sload), to_float_scaled(src[1], sload));
+                        }
                     }
                     // the edge node's populations from across the face (the box
                     // holds zero fill or a neighbour column there); nodes past
@@ -552,7 +573,7 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                         for (int q = 1; q < Q; ++q) {
                             if (L::c(q, 0) != 1 && L::c(q, 0) != -1) continue;
                             if (L::c(q, 0) != ecx) continue;
-                            const float vv = ev[r * QE + k];
+                            const float vv = FOLD ? ev[r * QE + k] * sstore_t : ev[r * QE + k];
                             ++k;
                             if (e == 0) f[q - 1].x = vv;
                             else f[q - 1].y = vv;
@@ -566,12 +587,15 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             const int xe = x + e;
-                            if (((rowok >> q) & 1u) && xe - cx >= 0 && xe - cx < nx)
-                                v[e] = to_float_scaled(rowbase[qoff(q) + lx + e - cx], sload);
-                            else
+                            if (((rowok >> q) & 1u) && xe - cx >= 0 && xe - cx < nx) {
+                                if constexpr (FOLD) v[e] = __half2float(rowbase[qoff(q) + lx + e - cx]);
+                                else v[e] = to_float_scaled(rowbase[qoff(q) + lx + e - cx], sload);
+                            } else {
                                 v[e] = xe < nx ? pull_scalar<Q, S>(insts[h.inst], static_cast<const S*>(h.ti.f[par]), q, xe,
                                                                      y, z)
                                                : 0.f;
+                                if constexpr (FOLD) v[e] *= sstore_t;
+                            }
                         }
                         f[q - 1] = make_float2(v[0], v[1]);
                     }
@@ -596,7 +620,8 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                     a[d] = add2(bc2(h.ti.gdrive[d]),
                                 make_float2(own0 >= 0 ? cand[sl0].a[d] : 0.f, own1 >= 0 ? cand[sl1].a[d] : 0.f));
                 float2 u[3], p;
-                collide2<Q>(f, a, own0 >= 0, own1 >= 0, ck, u, &p);
+                if constexpr (FOLD) collide2_t1_scaled<Q>(f, a, own0 >= 0, own1 >= 0, cks, sload, u, &p);
+                else collide2<Q>(f, a, own0 >= 0, own1 >= 0, ck, u, &p);
                 float2 uu = mul2(u[0], u[0]);
 #pragma unroll
                 for (int d = 1; d < D; ++d) uu = fma2(u[d], u[d], uu);
@@ -608,13 +633,15 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                     if (v1) {
 #pragma unroll
                         for (int q = 0; q < QS; ++q) {
-                            store_pair(o, f[q], sstore);
+                            if constexpr (FOLD) *reinterpret_cast<__half2*>(o) = __floats2half2_rn(f[q].x, f[q].y);
+                            else store_pair(o, f[q], sstore);
                             o += qs;
                         }
                     } else {
 #pragma unroll
                         for (int q = 0; q < QS; ++q) {
-                            *o = to_store<S>(f[q].x, sstore);
+                            if constexpr (FOLD) *o = __float2half_rn(f[q].x);
+                            else *o = to_store<S>(f[q].x, sstore);
                             o += qs;
                         }
                     }
@@ -625,6 +652,13 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
                 if (v1 && own1 >= 0)
                     box_store<D>(ubox, geo, cand[sl1], x + 1, y, z, u[0].y, u[1].y, D == 3 ? u[2].y : 0.f);
             }
+        }
+        };
+        if constexpr (sizeof(S) == 2 && Q == 9) {  // (D3Q19 would spill more)
+            if (ck.keep == 0.f) tile_rows(std::true_type{});
+            else tile_rows(std::false_type{});
+        } else {
+            tile_rows(std::false_type{});
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(h.ti.status, ST_DIVERGED);
         __syncwarp();
