@@ -376,7 +376,7 @@ def main():
             pinned.numpy()[:] = memoryview(blob)
             import ctypes
             npart = sum(sim.num_particles(i) for i in range(len(ws)))
-            ke = max(10, min(steps // 4, 1000))
+            ke = 1000  # a fixed run length, so that the one upload weighs the same whatever K
             # each step's result, the rigid-body state X, U, omega of every
             # particle, copied into pinned host buffers on the library's stream
             outs = [{k: torch.empty((sim.num_particles(i), 3), dtype=torch.float64, pin_memory=True).numpy()

@@ -1,4 +1,4 @@
-"""The allocation-free projection entry point against the context path.
+"""The allocation-free projection entry point against the context path and the oracle.
 
 lbm_rigid_projection_noalloc serves callers that cannot allocate device
 memory where they need the rigid-body projection (a host that owns all
@@ -112,6 +112,32 @@ def test_noalloc_projection_matches_context_path(D):
     case = _Case(D)
     for _ in range(2):  # two calls in a row share the scratch array
         case.assert_matches(case.call())
+
+
+@gpu
+@pytest.mark.parametrize("D", [2, 3])
+def test_noalloc_projection_matches_oracle(D):
+    """Eq. 22 against the FP64 oracle's projection of the same velocity field
+    over the same particles: equal node counts, and U, omega within the
+    fixed-point rounding of the exact sums (round(u 2^40) per node: at most
+    count * 2^-41 in sum u, so 2^-41 = 4.5e-13 in U; the same order in omega)."""
+    import oracle
+
+    case = _Case(D)
+    w = case.w
+    ref = oracle.Sim(oracle.make_config(D=D, n=w.n, periodic=w.periodic, tau=w.tau, alpha=w.alpha,
+                                        g_drive=w.g_drive, g_grav=w.g_grav))
+    ref.add_particles(case.pos.cpu().numpy(), w.radius, w.ratio)
+    u = np.moveaxis(case.u.cpu().numpy().astype(np.float64).reshape((D,) + ref.shape), 0, -1)
+    U, Wr, cnt = ref.rigid_projection(u)
+    ref.close()
+    rc, vel, om, c = case.call()
+    assert rc == 0, lbm.STATUS.get(rc, rc)
+    assert np.array_equal(c, cnt)
+    scale = np.abs(U[:, :D]).max()
+    assert np.abs(vel - U[:, :D]).max() <= 1e-9 * scale + 1e-12
+    Wref = Wr[:, 2:3] if D == 2 else Wr
+    assert np.abs(om - Wref).max() <= 1e-9 * np.abs(Wref).max() + 1e-12
 
 
 @gpu
