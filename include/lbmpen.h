@@ -210,8 +210,8 @@ int lbm_autotune(lbm_ctx* ctx, int reps);
  * filling a ring of shared-memory stages by tensor copies, `warps` consumer
  * warps, tile rows 4 or 8); vec = 1/2/4 (FP32) or 2/4/8 (FP16) is the
  * register path with vec nodes per thread and `warps` warps per block.
- * A new context starts in the TMA pipeline: D2Q9 with 8 rows, 8 warps and a
- * 3-stage ring, D3Q19 with 4 rows, 4 warps and a 2-stage ring.
+ * A new context starts in the TMA pipeline with a 2-stage ring: D2Q9 FP32
+ * with 8 rows and 8 warps, D2Q9 FP16 and D3Q19 with 4 rows and 4 warps.
  * lbm_set_kernel_shape keeps the current ring depth; lbm_autotune may change
  * it. */
 int lbm_kernel_shape(const lbm_ctx* ctx, int* vec, int* tile_rows, int* warps);

@@ -516,10 +516,12 @@ int configure_shape(lbm_ctx* ctx, const Shape& sh_in) {
 }
 
 Shape default_shape(int Q, int fp16) {
-    // TMA-staged pipeline: D2Q9 8 consumer warps, 2 stages for FP32 (one box
-    // of all populations per tile) and 3 for FP16; D3Q19 4 warps and 2 stages
-    // (four blocks per SM fit in shared memory, against three with 3)
-    if (Q == 9) return Shape{fp16 ? 8 : 4, 8, 1, 8, 1, 1, fp16 ? 3 : 2, 128};
+    // TMA-staged pipeline, 2 stages: D2Q9 FP32 8 rows and 8 consumer warps
+    // (one box of all populations per tile, two blocks per SM); D2Q9 FP16 4
+    // rows and 4 warps (four blocks per SM: 16 consumer warps, as for FP32,
+    // with tiles half as tall); D3Q19 4 warps (four blocks per SM fit in
+    // shared memory, against three with 3 stages)
+    if (Q == 9) return fp16 ? Shape{8, 4, 1, 4, 1, 1, 2, 128} : Shape{4, 8, 1, 8, 1, 1, 2, 128};
     return Shape{fp16 ? 4 : 2, 2, 2, 4, 1, 1, 2, 64};
 }
 
