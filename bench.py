@@ -17,9 +17,9 @@ import argparse
 import hashlib
 import json
 import os
+import select
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -85,7 +85,12 @@ def describe(name, ws, storage):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    One nvidia-smi process samples every 200 ms on its own (-lms), so no
+    Python thread of this process competes for the interpreter lock while the
+    timed region launches its work; the region starts right after the first
+    sample has arrived, and the process is stopped after the next one."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -94,29 +99,36 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.samples = []
-        self._stop = threading.Event()
-        self._t = None
+        self._p = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([v.strip() for v in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _take(self, line):
+        line = line.strip()
+        if line:
+            self.samples.append([v.strip() for v in line.split(",")])
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                        "--format=csv,noheader,nounits", "-lms", "200"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._take(self._p.stdout.readline())  # the first sample, just before the region
+        except Exception:
+            self._p = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is None:
+            return
+        try:
+            # one more sample, the first after the region (at most 1 s)
+            if select.select([self._p.stdout], [], [], 1.0)[0]:
+                self._take(self._p.stdout.readline())
+            self._p.terminate()
+            out, _ = self._p.communicate(timeout=10)
+            for line in out.splitlines():
+                self._take(line)
+        except Exception:
+            self._p.kill()
 
     def summary(self):
         if not self.samples:
