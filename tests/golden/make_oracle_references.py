@@ -28,6 +28,11 @@ GPU test suite (a 400 x 1600 oracle step takes ~30 ms on 8 cores):
       paper's shear time): every 200 steps the step count, X, Y, U_x, U_y,
       omega and the node count.
 
+  couette_migration_h40_long.txt
+      The same reduced Couette case run to 200,000 steps (gamma t = 417), every
+      2,000 steps: where the migration ends (the paper reports the disk at the
+      centre line y/H = 0.5).
+
   dkt_l200.txt
       Drafting, kissing and tumbling of two disks (Sec. 3.4; workloads.dkt):
       200 x 800 closed channel, D = 20, ratio 1.01, 12,000 steps: every 100
@@ -40,7 +45,7 @@ GPU test suite (a 400 x 1600 oracle step takes ~30 ms on 8 cores):
       steps: every 100 steps the step count, X, Y, U_x, U_y, omega, theta and
       the node count.
 
-  python tests/golden/make_oracle_references.py [trajectory|fd|couette|dkt|ellipse|all]
+  python tests/golden/make_oracle_references.py [trajectory|fd|couette|couette_long|dkt|ellipse|all]
 """
 import hashlib
 import os
@@ -57,6 +62,7 @@ from paper_2511_01629_gb300 import workloads as W  # noqa: E402
 
 TRAJ = os.path.join(HERE, "single_disk_seed0_trajectory.txt")
 COUETTE = os.path.join(HERE, "couette_migration_h40.txt")
+COUETTE_LONG = os.path.join(HERE, "couette_migration_h40_long.txt")
 DKT = os.path.join(HERE, "dkt_l200.txt")
 ELLIPSE = os.path.join(HERE, "ellipse_settling_l200.txt")
 FD = os.path.join(HERE, "adjoint_disk_seed0_fd.txt")
@@ -172,6 +178,17 @@ def couette():
         fh.write(text)
 
 
+def couette_long():
+    w = W.couette_migration(H=40, diameter=10.0, length_d=20.0, U_w=1.0 / 12.0, steps=200000)
+    text = _particle_rows(w, 2000, [
+        "# couette_migration H = 40, D = 10, L = 20 D, U_w = 1/12 (walls at -+U_w/2), tau = 1,\n",
+        "# rho_s = rho_f, disk released at (15 D, D - 1/2), 200,000 steps (gamma t = 417); FP64\n",
+        "# oracle (tests/golden/make_oracle_references.py); fluid at rest at step 0.\n",
+        "# step X Y U_x U_y omega count\n"])
+    with open(COUETTE_LONG, "w") as fh:
+        fh.write(text)
+
+
 def dkt():
     w = W.dkt()
     text = _particle_rows(w, 100, [
@@ -212,6 +229,8 @@ if __name__ == "__main__":
         finite_differences()
     if what in ("couette", "all"):
         couette()
+    if what in ("couette_long", "all"):
+        couette_long()
     if what in ("dkt", "all"):
         dkt()
     if what in ("ellipse", "all"):

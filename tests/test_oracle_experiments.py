@@ -6,7 +6,8 @@ by what the physics fixes rather than by the oracle itself:
     (L - x0, H - 1 - y0) follow trajectories that are each other's half
     turn: X' = L - X, Y' = H - 1 - Y, U' = -U, omega' = omega;
   * a neutrally buoyant disk released off centre in Couette flow migrates
-    towards the centre line (Sec. 3.1) and, free of torque, turns at about
+    towards the centre line and comes to rest there (Sec. 3.1) and, free of
+    torque, turns at about
     half the shear rate, omega = -gamma / 2 (the rotation of a free circle in
     simple shear; the walls 1.5 D away slow it slightly);
   * two disks released one above the other draft, kiss and tumble
@@ -121,6 +122,31 @@ def test_couette_disk_migrates_to_the_centre_line():
     assert -0.575 < w_over_g.mean() < -0.425, w_over_g.mean()
     # the node count stays that of a disk R = 5 (pi R^2 = 78.5)
     assert np.all(np.abs(r[1:, 6] - np.pi * 25) < 6)
+
+
+def test_couette_disk_comes_to_rest_at_the_centre_line():
+    """The same case run to gamma t = 417: the migration ends at the centre
+    line (Sec. 3.1).  y/H rises in every window of gamma t ~ 21 until it is
+    within 0.01 of 0.5, then stays on a plateau from gamma t ~ 170 on; the
+    plateau lies less than one lattice unit below the centre line (the
+    staircase of a D = 10 disk on the lattice shifts its equilibrium by a
+    fraction of a node) and jitters by less than 0.1 node as the disk's node
+    set changes with its x position.  The run is bit for bit the short stored
+    run over their common rows."""
+    r = _load("couette_migration_h40_long.txt")
+    short = _load("couette_migration_h40.txt")
+    common = short[np.isin(short[:, 0], r[:, 0])]
+    assert len(common) == 15 and np.array_equal(common, r[: len(common)])
+    H = 40
+    yH = (r[:, 2] + 0.5) / H
+    rising = yH[yH < 0.49]
+    assert np.all(np.diff(rising[::5]) > 0), rising[::5]
+    plateau = yH[r[:, 0] >= 80000]
+    assert np.all(np.abs(plateau - 0.5) < 1.0 / H), plateau.min()
+    assert np.all(plateau < 0.5)
+    assert plateau.max() - plateau.min() < 0.1 / H
+    # settled: the lateral velocity averages to zero on the plateau
+    assert abs(r[r[:, 0] >= 80000, 4].mean()) < 2e-5
 
 
 def test_dkt_reference_drafts_kisses_and_tumbles():
