@@ -520,139 +520,140 @@ __global__ void __launch_bounds__(288, 2) k_fluid_tma(const InstDesc* __restrict
         // FOLD (D2Q9, FP16 storage at tau = 1): the populations stay at the
         // storage scale from the stage to the store (collide2_t1_scaled)
         auto tile_rows = [&](auto fold_tag) {
-        constexpr bool FOLD = decltype(fold_tag)::value;
-        CollK cks = ck;
-        if constexpr (FOLD) {
+            constexpr bool FOLD = decltype(fold_tag)::value;
+            CollK cks = ck;
+            if constexpr (FOLD) {
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                cks.A[i] *= sstore_t;
-                cks.fA[i] *= sstore_t;
-                cks.sA[i] *= sstore_t;
+                for (int i = 0; i < 2; ++i) {
+                    cks.A[i] *= sstore_t;
+                    cks.fA[i] *= sstore_t;
+                    cks.sA[i] *= sstore_t;
+                }
             }
-        }
-        for (int r = cw; r < rows; r += nc) {
-            const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
-            if (y >= ny || z >= nz) continue;
-            // populations whose source row lies inside the staged box
-            unsigned rowok = 0;
+            for (int r = cw; r < rows; r += nc) {
+                const int y = y0 + r % sh.ty, z = z0 + r / sh.ty;
+                if (y >= ny || z >= nz) continue;
+                // populations whose source row lies inside the staged box
+                unsigned rowok = 0;
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                const int ys = y - L::c(q, 1), zs = z - L::c(q, 2);
-                if (ys >= 0 && ys < ny && zs >= 0 && zs < nz) rowok |= 1u << q;
-            }
-            const bool rowfast = rowok == (((1u << Q) - 1) & ~1u);
-            const S* rowbase = stage + r * BW + H;
-            // element of population q's source row in the stage, relative to rowbase
-            auto qoff = [&](int q) { return (q - 1) * SLAB + (Q == 9 ? (1 - L::c(q, 1)) * BW : 0); };
-            S* outrow = static_cast<S*>(const_cast<void*>(h.ti.f[par ^ 1])) + ((long long)z * ny + y) * h.ti.pitch;
-            // two adjacent nodes per lane: packed FP32x2 arithmetic, 8-byte stores
-            for (int j = 0; j < TW / 64; ++j) {
-                const int lx = j * 64 + 2 * lane;
-                const int x = x0 + lx;
-                const bool v0 = x < nx, v1 = x + 1 < nx;
-                float2 f[QS];
-                if (rowfast && (ex >= 0 || __all_sync(0xffffffffu, x > 0 && x + 1 < nx - 1))) {
-#pragma unroll
-                    for (int q = 1; q < Q; ++q) {
-                        const S* src = rowbase + qoff(q) + lx - L::c(q, 0);
-                        if constexpr (FOLD) {
-                            if (L::c(q, 0) == 0) f[q - 1] = __half22float2(*reinterpret_cast<const __half2*>(src));
-                            else f[q - 1] = make_float2(__half2float(src[0]), __half2float(src[1]));
-                        } else {
-                            if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, sload);
-                            else f[q - 1] = make_float2(to_float_scaled(src[0], sload), to_float_scaled(src[1], sload));
-                        }
-                    }
-                    // the edge node's populations from across the face (the box
-                    // holds zero fill or a neighbour column there); nodes past
-                    // nx in a ragged tile are computed but never stored
-                    const int e = ex - x;
-                    if (ex >= 0 && (e == 0 || e == 1)) {
-                        int k = 0;
+                for (int q = 1; q < Q; ++q) {
+                    const int ys = y - L::c(q, 1), zs = z - L::c(q, 2);
+                    if (ys >= 0 && ys < ny && zs >= 0 && zs < nz) rowok |= 1u << q;
+                }
+                const bool rowfast = rowok == (((1u << Q) - 1) & ~1u);
+                const S* rowbase = stage + r * BW + H;
+                // element of population q's source row in the stage, relative to rowbase
+                auto qoff = [&](int q) { return (q - 1) * SLAB + (Q == 9 ? (1 - L::c(q, 1)) * BW : 0); };
+                S* outrow = static_cast<S*>(const_cast<void*>(h.ti.f[par ^ 1])) + ((long long)z * ny + y) * h.ti.pitch;
+                // two adjacent nodes per lane: packed FP32x2 arithmetic, 8-byte stores
+                for (int j = 0; j < TW / 64; ++j) {
+                    const int lx = j * 64 + 2 * lane;
+                    const int x = x0 + lx;
+                    const bool v0 = x < nx, v1 = x + 1 < nx;
+                    float2 f[QS];
+                    if (rowfast && (ex >= 0 || __all_sync(0xffffffffu, x > 0 && x + 1 < nx - 1))) {
 #pragma unroll
                         for (int q = 1; q < Q; ++q) {
-                            if (L::c(q, 0) != 1 && L::c(q, 0) != -1) continue;
-                            if (L::c(q, 0) != ecx) continue;
-                            const float vv = FOLD ? ev[r * QE + k] * sstore_t : ev[r * QE + k];
-                            ++k;
-                            if (e == 0) f[q - 1].x = vv;
-                            else f[q - 1].y = vv;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 1; q < Q; ++q) {
-                        const int cx = L::c(q, 0);
-                        float v[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int xe = x + e;
-                            if (((rowok >> q) & 1u) && xe - cx >= 0 && xe - cx < nx) {
-                                if constexpr (FOLD) v[e] = __half2float(rowbase[qoff(q) + lx + e - cx]);
-                                else v[e] = to_float_scaled(rowbase[qoff(q) + lx + e - cx], sload);
+                            const S* src = rowbase + qoff(q) + lx - L::c(q, 0);
+                            if constexpr (FOLD) {
+                                if (L::c(q, 0) == 0) f[q - 1] = __half22float2(*reinterpret_cast<const __half2*>(src));
+                                else f[q - 1] = make_float2(__half2float(src[0]), __half2float(src[1]));
                             } else {
-                                v[e] = xe < nx ? pull_scalar<Q, S>(insts[h.inst], static_cast<const S*>(h.ti.f[par]), q, xe,
-                                                                     y, z)
-                                               : 0.f;
-                                if constexpr (FOLD) v[e] *= sstore_t;
+                                if (L::c(q, 0) == 0) f[q - 1] = smem_pair(src, sload);
+                                else
+                                    f[q - 1] = make_float2(to_float_scaled(src[0], sload),
+                                                           to_float_scaled(src[1], sload));
                             }
                         }
-                        f[q - 1] = make_float2(v[0], v[1]);
-                    }
-                }
-                const int xyz0[3] = {x, y, z}, xyz1[3] = {x + 1, y, z};
-                int own0 = -1, own1 = -1, sl0 = -1, sl1 = -1;
-                unsigned act = 0;
-                if (ncand > 32) {  // more candidates than mask bits: test them all
-                    act = 0xffffffffu;
-                    own0 = owner_of<D>(geo, cand, ncand, xyz0, &sl0);
-                    own1 = owner_of<D>(geo, cand, ncand, xyz1, &sl1);
-                } else if (ncand > 0) {
-                    act = segment_candidates<D>(geo, cand, ncand, x0 + j * 64, y, z, 64, lane);
-                    if (act) {
-                        own0 = owner_masked<D>(geo, cand, act, xyz0, &sl0);
-                        own1 = owner_masked<D>(geo, cand, act, xyz1, &sl1);
-                    }
-                }
-                float2 a[3];
+                        // the edge node's populations from across the face (the box
+                        // holds zero fill or a neighbour column there); nodes past
+                        // nx in a ragged tile are computed but never stored
+                        const int e = ex - x;
+                        if (ex >= 0 && (e == 0 || e == 1)) {
+                            int k = 0;
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    a[d] = add2(bc2(h.ti.gdrive[d]),
-                                make_float2(own0 >= 0 ? cand[sl0].a[d] : 0.f, own1 >= 0 ? cand[sl1].a[d] : 0.f));
-                float2 u[3], p;
-                if constexpr (FOLD) collide2_t1_scaled<Q>(f, a, own0 >= 0, own1 >= 0, cks, sload, u, &p);
-                else collide2<Q>(f, a, own0 >= 0, own1 >= 0, ck, u, &p);
-                float2 uu = mul2(u[0], u[0]);
-#pragma unroll
-                for (int d = 1; d < D; ++d) uu = fma2(u[d], u[d], uu);
-                bad |= (v0 && !(uu.x < 0.25f)) || (v1 && !(uu.y < 0.25f));
-                if (v0) {
-                    S* o = outrow + x;
-                    const int qs = (int)h.ti.qstride;  // < 2^31 elements per population
-                    const float sstore = h.ti.sstore;
-                    if (v1) {
-#pragma unroll
-                        for (int q = 0; q < QS; ++q) {
-                            if constexpr (FOLD) *reinterpret_cast<__half2*>(o) = __floats2half2_rn(f[q].x, f[q].y);
-                            else store_pair(o, f[q], sstore);
-                            o += qs;
+                            for (int q = 1; q < Q; ++q) {
+                                if (L::c(q, 0) != 1 && L::c(q, 0) != -1) continue;
+                                if (L::c(q, 0) != ecx) continue;
+                                const float vv = FOLD ? ev[r * QE + k] * sstore_t : ev[r * QE + k];
+                                ++k;
+                                if (e == 0) f[q - 1].x = vv;
+                                else f[q - 1].y = vv;
+                            }
                         }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < QS; ++q) {
-                            if constexpr (FOLD) *o = __float2half_rn(f[q].x);
-                            else *o = to_store<S>(f[q].x, sstore);
-                            o += qs;
+                        for (int q = 1; q < Q; ++q) {
+                            const int cx = L::c(q, 0);
+                            float v[2];
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const int xe = x + e;
+                                if (((rowok >> q) & 1u) && xe - cx >= 0 && xe - cx < nx) {
+                                    if constexpr (FOLD) v[e] = __half2float(rowbase[qoff(q) + lx + e - cx]);
+                                    else v[e] = to_float_scaled(rowbase[qoff(q) + lx + e - cx], sload);
+                                } else {
+                                    const S* fin = static_cast<const S*>(h.ti.f[par]);
+                                    v[e] = xe < nx ? pull_scalar<Q, S>(insts[h.inst], fin, q, xe, y, z) : 0.f;
+                                    if constexpr (FOLD) v[e] *= sstore_t;
+                                }
+                            }
+                            f[q - 1] = make_float2(v[0], v[1]);
                         }
                     }
+                    const int xyz0[3] = {x, y, z}, xyz1[3] = {x + 1, y, z};
+                    int own0 = -1, own1 = -1, sl0 = -1, sl1 = -1;
+                    unsigned act = 0;
+                    if (ncand > 32) {  // more candidates than mask bits: test them all
+                        act = 0xffffffffu;
+                        own0 = owner_of<D>(geo, cand, ncand, xyz0, &sl0);
+                        own1 = owner_of<D>(geo, cand, ncand, xyz1, &sl1);
+                    } else if (ncand > 0) {
+                        act = segment_candidates<D>(geo, cand, ncand, x0 + j * 64, y, z, 64, lane);
+                        if (act) {
+                            own0 = owner_masked<D>(geo, cand, act, xyz0, &sl0);
+                            own1 = owner_masked<D>(geo, cand, act, xyz1, &sl1);
+                        }
+                    }
+                    float2 a[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        a[d] = add2(bc2(h.ti.gdrive[d]),
+                                    make_float2(own0 >= 0 ? cand[sl0].a[d] : 0.f, own1 >= 0 ? cand[sl1].a[d] : 0.f));
+                    float2 u[3], p;
+                    if constexpr (FOLD) collide2_t1_scaled<Q>(f, a, own0 >= 0, own1 >= 0, cks, sload, u, &p);
+                    else collide2<Q>(f, a, own0 >= 0, own1 >= 0, ck, u, &p);
+                    float2 uu = mul2(u[0], u[0]);
+#pragma unroll
+                    for (int d = 1; d < D; ++d) uu = fma2(u[d], u[d], uu);
+                    bad |= (v0 && !(uu.x < 0.25f)) || (v1 && !(uu.y < 0.25f));
+                    if (v0) {
+                        S* o = outrow + x;
+                        const int qs = (int)h.ti.qstride;  // < 2^31 elements per population
+                        const float sstore = h.ti.sstore;
+                        if (v1) {
+#pragma unroll
+                            for (int q = 0; q < QS; ++q) {
+                                if constexpr (FOLD) *reinterpret_cast<__half2*>(o) = __floats2half2_rn(f[q].x, f[q].y);
+                                else store_pair(o, f[q], sstore);
+                                o += qs;
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < QS; ++q) {
+                                if constexpr (FOLD) *o = __float2half_rn(f[q].x);
+                                else *o = to_store<S>(f[q].x, sstore);
+                                o += qs;
+                            }
+                        }
+                    }
+                    // the solid nodes' velocities into their particles' boxes (Eq. 22)
+                    if (v0 && own0 >= 0)
+                        box_store<D>(ubox, geo, cand[sl0], x, y, z, u[0].x, u[1].x, D == 3 ? u[2].x : 0.f);
+                    if (v1 && own1 >= 0)
+                        box_store<D>(ubox, geo, cand[sl1], x + 1, y, z, u[0].y, u[1].y, D == 3 ? u[2].y : 0.f);
                 }
-                // the solid nodes' velocities into their particles' boxes (Eq. 22)
-                if (v0 && own0 >= 0)
-                    box_store<D>(ubox, geo, cand[sl0], x, y, z, u[0].x, u[1].x, D == 3 ? u[2].x : 0.f);
-                if (v1 && own1 >= 0)
-                    box_store<D>(ubox, geo, cand[sl1], x + 1, y, z, u[0].y, u[1].y, D == 3 ? u[2].y : 0.f);
             }
-        }
         };
         if constexpr (sizeof(S) == 2 && Q == 9) {  // (D3Q19 would spill more)
             if (ck.keep == 0.f) tile_rows(std::true_type{});
