@@ -714,12 +714,15 @@ __global__ void k_adj_state(const InstDesc* __restrict__ insts, int inst, double
 cudaError_t launch_adj_fluid(int Q, int fp16, const InstDesc* insts, const AdjFluid* afs,
                              const uint16_t* tile_inst, int ntiles, int lam_mode, const Shape& sh,
                              cudaStream_t st) {
+    // a warp per tile row, up to the 8 warps of the launch bounds
+    const int rows = sh.ty * sh.tz;
+    const int threads = 32 * (rows < 8 ? rows : 8);
     if (Q == 9) {
-        if (fp16) k_adj_fluid<9, __half><<<ntiles, 256, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
-        else k_adj_fluid<9, float><<<ntiles, 256, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
+        if (fp16) k_adj_fluid<9, __half><<<ntiles, threads, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
+        else k_adj_fluid<9, float><<<ntiles, threads, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
     } else {
-        if (fp16) k_adj_fluid<19, __half><<<ntiles, 256, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
-        else k_adj_fluid<19, float><<<ntiles, 256, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
+        if (fp16) k_adj_fluid<19, __half><<<ntiles, threads, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
+        else k_adj_fluid<19, float><<<ntiles, threads, 0, st>>>(insts, afs, tile_inst, lam_mode, sh);
     }
     return cudaGetLastError();
 }
